@@ -1,0 +1,381 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself.
+
+Each test names the passage of the paper it checks and the external fact it
+checks against (a library routine, a closed form, a hand-derived linearisation,
+brute force, or a Monte-Carlo bound on an exact Kalman posterior).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import enkf, metrics
+import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ---------------------------------------------------------------- Philox ----
+def _numpy_philox(ctr, key):
+    """numpy's Philox (4x64-10) increments its 256-bit counter before each
+    block, so block(ctr) is what numpy returns from counter ctr - 1."""
+    c = [int(x) for x in ctr]
+    for i in range(4):
+        if c[i] > 0:
+            c[i] -= 1
+            break
+        c[i] = 2**64 - 1
+    bg = np.random.Philox(counter=np.array(c, dtype=np.uint64), key=np.array(key, dtype=np.uint64))
+    return np.array(bg.random_raw(4), dtype=np.uint64)
+
+
+def test_philox_matches_numpy_library():
+    rng = np.random.default_rng(1)
+    cases = [((0, 0, 0, 0), (0, 0)), ((1, 0, 0, 0), (0, 0)),
+             ((2**64 - 1,) * 4, (2**64 - 1,) * 2), ((12345, 678, 1, 0), (15964, 3))]
+    for _ in range(20):
+        cases.append((tuple(int(x) for x in rng.integers(0, 2**63, 4, dtype=np.uint64)),
+                      tuple(int(x) for x in rng.integers(0, 2**63, 2, dtype=np.uint64))))
+    for ctr, key in cases:
+        assert np.array_equal(oracle.philox4x64(ctr, key), _numpy_philox(ctr, key)), (ctr, key)
+
+
+# ------------------------------------------------------ Poisson drive -------
+@pytest.mark.parametrize("lam", [0.0, 1e-3, 0.05, 0.5, 2.0])
+def test_poisson_thresholds_match_scipy_cdf(lam):
+    from scipy.stats import poisson
+    thr = oracle.poisson_thresholds(lam)
+    ref = []
+    for k in range(16):
+        t = math.floor(poisson.cdf(k, lam) * 2**32)
+        if t >= 2**32:
+            break
+        ref.append(t)
+    assert len(thr) == len(ref)
+    assert np.all(np.abs(thr.astype(np.int64) - np.array(ref, dtype=np.int64)) <= 1)
+
+
+def test_poisson_inversion_counts_follow_pmf():
+    from scipy.stats import poisson
+    lam = 0.7
+    thr = oracle.poisson_thresholds(lam).astype(np.uint64)
+    u = np.random.default_rng(2).integers(0, 2**32, 2_000_000, dtype=np.uint64)
+    c = (u[:, None] >= thr[None, :]).sum(axis=1)
+    n = len(u)
+    obs = np.bincount(c, minlength=8)[:6]
+    exp = poisson.pmf(np.arange(6), lam) * n
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    assert chi2 < 30.0  # 5 dof; p < 1e-5 above this
+    assert abs(c.mean() - lam) < 5 * math.sqrt(lam / n)
+
+
+# ---------------------------------------------------------------- LIF -------
+def _iso_graph(n=4, exc_frac=0.8):
+    W = np.zeros((n, n))
+    return synth.graph_from_dense(W, np.ones((n, n), dtype=np.int64), [n], exc_frac)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("case", [
+    dict(dt=0.1, C=0.5, gL=0.025, I=0.6, Tref=2.0),
+    dict(dt=0.05, C=0.25, gL=0.03, I=0.7, Tref=1.5),
+])
+def test_lif_interspike_interval_closed_form(precision, case):
+    """Methods capacitance-voltage equation + Supp. Eq. 5 reset: under a
+    constant current the discrete scheme is a linear recursion
+    V' - Vinf = a (V - Vinf), a = 1 - dt gL / C, Vinf = VL + I/gL, so from
+    V_reset the k-th free step crosses V_th for the first k >= k*,
+    k* = ln((Vinf - Vth)/(Vinf - Vreset)) / ln a, and the period is n_ref + k."""
+    p = synth.default_region_params(C=case["C"], gL=case["gL"], I_ext=case["I"], drive_rate_hz=0.0,
+                                    Tref=case["Tref"], g_u=(0.0, 0.0, 0.0, 0.0))
+    dt = case["dt"]
+    a = 1.0 - dt * p["gL"] / p["C"]
+    Vinf = p["VL"] + p["I_ext"] / p["gL"]
+    kstar = math.log((Vinf - p["Vth"]) / (Vinf - p["Vreset"])) / math.log(a)
+    assert 0.05 < kstar - math.floor(kstar) < 0.95  # away from a rounding tie
+    k = math.ceil(kstar)
+    n_ref = round(p["Tref"] / dt)
+    g = _iso_graph()
+    s = oracle.Sim(g, p, dt_ms=dt, bin_ms=1.0, precision=precision)
+    s.set_state(V=np.full(4, p["Vreset"]), J=np.zeros((4, 4)), ref=np.zeros(4, np.int32))
+    T = 5 * (n_ref + k) + 3
+    s.step(T)
+    st, ids = s.raster()
+    first = st[ids == 0]
+    expect = np.arange(k - 1, T, n_ref + k)
+    assert np.array_equal(first, expect)
+
+
+def test_lif_continuous_limit():
+    """As dt -> 0 the discrete period approaches T_ref + tau_m ln((Vinf - Vreset)/(Vinf - Vth))."""
+    p = synth.default_region_params(I_ext=0.6, drive_rate_hz=0.0, g_u=(0.0, 0.0, 0.0, 0.0))
+    tau_m = p["C"] / p["gL"]
+    Vinf = p["VL"] + p["I_ext"] / p["gL"]
+    T_cont = p["Tref"] + tau_m * math.log((Vinf - p["Vreset"]) / (Vinf - p["Vth"]))
+    dt = 0.002
+    g = _iso_graph()
+    s = oracle.Sim(g, p, dt_ms=dt, bin_ms=1.0, precision=64)
+    s.set_state(V=np.full(4, p["Vreset"]), J=np.zeros((4, 4)), ref=np.zeros(4, np.int32))
+    s.step(int(3 * T_cont / dt))
+    st, ids = s.raster()
+    period = np.diff(st[ids == 0]).mean() * dt
+    assert abs(period - T_cont) < 2 * dt + 1e-3 * T_cont
+
+
+# -------------------------------------------------- synaptic traces ---------
+@pytest.mark.parametrize("exc_frac,channels", [(1.0, (0, 1)), (0.0, (2, 3))])
+def test_trace_arrival_and_exponential_decay(exc_frac, channels):
+    """Supp. Eq. 3: J(t+dt) = exp(-dt/tau) J(t) + w A(t).  A spike of neuron 0
+    at step 0 over an edge of delay 3 reaches neuron 1's traces of the
+    source's class at step 3; afterwards J_n = w exp(-dt/tau)^n."""
+    W = np.zeros((2, 2))
+    W[1, 0] = 0.75
+    Dl = np.full((2, 2), 3)
+    g = synth.graph_from_dense(W, Dl, [2], exc_frac)
+    p = synth.default_region_params(I_ext=0.0, drive_rate_hz=0.0)
+    s = oracle.Sim(g, p, precision=64)
+    s.set_state(V=np.array([-49.0, -70.0]), J=np.zeros((4, 2)), ref=np.zeros(2, np.int32))
+    traj = []
+    for _ in range(200):
+        s.step(1)
+        traj.append(s.state()[1][:, 1].copy())
+    traj = np.array(traj)  # [step, channel]
+    st, ids = s.raster()
+    assert list(zip(st, ids)) == [(0, 0)]
+    assert np.all(traj[:3] == 0.0)
+    other = [u for u in range(4) if u not in channels]
+    assert np.all(traj[:, other] == 0.0)
+    for u in channels:
+        dec = math.exp(-0.1 / p["tau_u"][u])
+        m = np.arange(197)
+        expect = 0.75 * dec ** m
+        assert np.allclose(traj[3:, u], expect, rtol=1e-13, atol=0)
+
+
+def test_conductance_steady_state():
+    """Methods, I_u = g_u (V_u - V) J_u with frozen traces: V converges to
+    (gL VL + sum g J V_u + I) / (gL + sum g J)."""
+    p = synth.default_region_params(I_ext=0.05, drive_rate_hz=0.0, Vth=100.0,
+                                    tau_u=(1e300,) * 4, g_u=(0.01, 0.002, 0.03, 0.004))
+    g = _iso_graph()
+    s = oracle.Sim(g, p, precision=64)
+    J = np.array([[0.8] * 4, [5.0] * 4, [0.6] * 4, [2.0] * 4])
+    s.set_state(V=np.full(4, -60.0), J=J, ref=np.zeros(4, np.int32))
+    s.step(40000)
+    V = s.state()[0]
+    gJ = np.array(p["g_u"]) * J[:, 0]
+    Vss = (p["gL"] * p["VL"] + (gJ * np.array(p["Vu"])).sum() + p["I_ext"]) / (p["gL"] + gJ.sum())
+    assert np.allclose(V, Vss, rtol=1e-9)
+
+
+# ------------------------------------------------------------ delivery ------
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_delivery_matches_brute_force_all_pairs(seed):
+    """Supp. Algorithm 2 (push delivery) against a dense all-pairs sum:
+    ring[(n + d_ij) mod D][i][class j] = sum over spiking j of q(W_ij)."""
+    rng = np.random.default_rng(seed)
+    sizes = [60, 36]
+    N = sum(sizes)
+    W = np.where(rng.random((N, N)) < 0.3, np.exp(rng.normal(-1, 0.5, (N, N))), 0.0)
+    np.fill_diagonal(W, 0.0)
+    W = synth.bf16_to_f64(synth.f64_to_bf16(W))
+    Dl = rng.integers(1, 8, (N, N))
+    g = synth.graph_from_dense(W, Dl, sizes)
+    p = synth.default_region_params(drive_rate_hz=0.0)
+    s = oracle.Sim(g, p, precision=32)
+    info = s.info()
+    D, S = info["D"], info["S"]
+    exc = np.zeros(N, dtype=bool)
+    for r in range(len(sizes)):
+        exc[g.region_offsets[r]:g.region_offsets[r] + g.n_exc[r]] = True
+    expect = np.zeros((D, N, 2), dtype=np.int64)
+    total = 0
+    for call in range(4):
+        n = int(rng.integers(0, 50))
+        ids = np.sort(rng.choice(N, size=int(rng.integers(1, 20)), replace=False)).astype(np.int32)
+        s.deliver_only(ids, n)
+        for i in range(N):
+            for j in ids:
+                if W[i, j] != 0.0:
+                    expect[(n + Dl[i, j]) % D, i, 0 if exc[j] else 1] += int(np.rint(W[i, j] * 2.0**S))
+                    total += 1
+    assert np.array_equal(s.ring(), expect)
+    assert s.info()["events"] == total
+
+
+def test_events_equal_spikes_times_out_degree(small_graph):
+    """Every spike delivers exactly its out-degree (Supp. Algorithm 2)."""
+    s = oracle.Sim(small_graph, synth.default_region_params(), seed=15964, precision=32)
+    s.step(300)
+    st, ids = s.raster()
+    outdeg = np.diff(small_graph.row_ptr)
+    info = s.info()
+    assert info["spikes"] == len(ids) > 0
+    assert info["events"] == int(outdeg[ids].sum())
+
+
+# ---------------------------------------------------- Balloon-Windkessel ----
+def test_bw_rest_is_exact_fixed_point():
+    """Extended Data Table 4 with z = 0 from s=0, f=v=q=1: every derivative is
+    zero exactly (E(1, rho) = rho) and y = 0."""
+    x = np.array([0.0, 1.0, 1.0, 1.0])
+    for _ in range(1000):
+        y = oracle.bw_step(x, 0.0, 1e-3, synth.BW_DEFAULT)
+        assert y == 0.0
+    assert np.array_equal(x, [0.0, 1.0, 1.0, 1.0])
+
+
+@pytest.mark.parametrize("z", [0.005, 0.02, 0.1])
+def test_bw_constant_input_fixed_point(z):
+    """Closed-form fixed point for constant z: s* = 0, f* = 1 + z/gamma,
+    v* = f*^alpha, q* = v* E(f*, rho)/rho, y* from the BOLD equation."""
+    bw = synth.BW_DEFAULT
+    x = np.array([0.0, 1.0, 1.0, 1.0])
+    for _ in range(300_000):
+        y = oracle.bw_step(x, z, 1e-3, bw)
+    f = 1 + z / bw["gamma"]
+    v = f ** bw["alpha"]
+    q = v * (1 - (1 - bw["rho"]) ** (1 / f)) / bw["rho"]
+    k1, k2, k3 = 7 * bw["rho"], 2.0, 2 * bw["rho"] - 0.2
+    ystar = bw["V0"] * (k1 * (1 - q) + k2 * (1 - q / v) + k3 * (1 - v))
+    assert np.allclose(x, [0.0, f, v, q], rtol=1e-7, atol=1e-9)
+    assert abs(y - ystar) <= 1e-7 * abs(ystar)
+
+
+def test_bw_linear_response_matches_hand_jacobian():
+    """Small-signal response against the Jacobian of Extended Data Table 4 at
+    rest, derived by hand: E'(1) = (1 - rho) ln(1 - rho)."""
+    bw = synth.BW_DEFAULT
+    ka, ga, ta, al, rho, V0 = (bw[k] for k in ("kappa", "gamma", "tau", "alpha", "rho", "V0"))
+    A = np.zeros((4, 4))
+    A[0, 0], A[0, 1] = -ka, -ga
+    A[1, 0] = 1.0
+    A[2, 1], A[2, 2] = 1 / ta, -1 / (al * ta)
+    A[3, 1] = (rho + (1 - rho) * math.log(1 - rho)) / rho / ta
+    A[3, 2] = -(1 / al - 1) / ta
+    A[3, 3] = -1 / ta
+    B = np.array([1.0, 0, 0, 0])
+    c = V0 * np.array([0.0, 0.0, (2.0 - (2 * rho - 0.2)), -(7 * rho + 2.0)])
+    h, eps = 1e-3, 1e-6
+    x = np.array([0.0, 1.0, 1.0, 1.0])
+    dx = np.zeros(4)
+    y_or, y_lin = [], []
+    for k in range(20000):
+        z = eps if k < 200 else 0.0
+        y_or.append(oracle.bw_step(x, z, h, bw))
+        dx = dx + h * (A @ dx + B * z)
+        y_lin.append(c @ dx)
+    y_or, y_lin = np.array(y_or), np.array(y_lin)
+    assert np.max(np.abs(y_or - y_lin)) < 1e-4 * np.max(np.abs(y_lin))
+
+
+# ---------------------------------------------------------------- EnKF ------
+def _prior(R, rng, block_diag=False):
+    n = enkf.BLOCK * R
+    G = rng.normal(size=(n, n)) * 0.3
+    if block_diag:
+        mask = np.kron(np.eye(R), np.ones((enkf.BLOCK, enkf.BLOCK)))
+        G = G * mask
+    P = G @ G.T + 0.2 * np.eye(n)
+    mu = rng.normal(size=n)
+    return mu, P
+
+
+def test_enkf_global_mode_matches_exact_kalman_posterior():
+    """Textbook stochastic EnKF (one observer, all regions): as M grows the
+    analysis mean and covariance approach the exact linear-Gaussian
+    posterior mu + P H^T (H P H^T + G)^-1 (y - H mu), (I - K H) P."""
+    rng = np.random.default_rng(5)
+    R, M, obs_var = 2, 40000, 0.5
+    mu, P = _prior(R, rng)
+    n = len(mu)
+    X = rng.multivariate_normal(mu, P, size=M)
+    y = rng.normal(size=R) * 2
+    eps = rng.normal(size=(M, R))
+    Xa = enkf.diffusion_enkf(X, y, obs_var, 1.0, eps, mode="global")
+    H = np.zeros((R, n))
+    for r in range(R):
+        H[r, enkf.BLOCK * r + enkf.Y_INDEX] = 1
+    K = P @ H.T @ np.linalg.inv(H @ P @ H.T + obs_var * np.eye(R))
+    mu_a = mu + K @ (y - H @ mu)
+    P_a = (np.eye(n) - K @ H) @ P
+    sd = np.sqrt(np.diag(P))
+    assert np.all(np.abs(Xa.mean(0) - mu_a) < 8 * sd / np.sqrt(M) * (1 + np.abs(y - H @ mu).max()))
+    Pa_hat = np.cov(Xa.T)
+    assert np.allclose(np.diag(Pa_hat), np.diag(P_a), rtol=0.06, atol=0.01)
+
+
+def test_enkf_diffusion_fusion_weights_own_observer_by_gamma():
+    """Supp. Algorithm 3 step 7 with independent regions: the other observers'
+    gains on block b vanish, so block b moves by gamma times its own exact
+    single-observer correction."""
+    rng = np.random.default_rng(6)
+    R, M, obs_var, gamma = 3, 40000, 0.3, 0.7
+    mu, P = _prior(R, rng, block_diag=True)
+    X = rng.multivariate_normal(mu, P, size=M)
+    y = mu[[enkf.BLOCK * r + enkf.Y_INDEX for r in range(R)]] + rng.normal(size=R)
+    eps = rng.normal(size=(M, R))
+    Xa = enkf.diffusion_enkf(X, y, obs_var, gamma, eps)
+    for b in range(R):
+        h = enkf.BLOCK * b + enkf.Y_INDEX
+        blk = slice(enkf.BLOCK * b, enkf.BLOCK * (b + 1))
+        K = P[blk, h] / (P[h, h] + obs_var)
+        expect = mu[blk] + gamma * K * (y[b] - mu[h])
+        sd = np.sqrt(np.diag(P)[blk])
+        assert np.all(np.abs(Xa.mean(0)[blk] - expect) < 10 * sd / np.sqrt(M) * (1 + abs(y[b] - mu[h])))
+
+
+def test_enkf_perfect_observation_and_no_information_limits():
+    rng = np.random.default_rng(7)
+    R, M = 4, 64
+    mu, P = _prior(R, rng)
+    X = rng.multivariate_normal(mu, P, size=M)
+    y = rng.normal(size=R)
+    zero = np.zeros((M, R))
+    # Gamma -> 0, gamma = 1: every observed BOLD value lands on the observation
+    Xa = enkf.diffusion_enkf(X, y, 1e-14, 1.0, zero)
+    for r in range(R):
+        assert np.allclose(Xa[:, enkf.BLOCK * r + enkf.Y_INDEX], y[r], atol=1e-9)
+    # Gamma -> infinity: nothing moves
+    Xb = enkf.diffusion_enkf(X, y, 1e14, 0.6, rng.normal(size=(M, R)))
+    assert np.allclose(Xb, X, atol=1e-5)
+
+
+def test_enkf_single_observer_is_textbook_enkf():
+    """With one region the diffusion filter has one observer and is the
+    textbook stochastic EnKF (the global mode)."""
+    rng = np.random.default_rng(8)
+    mu, P = _prior(1, rng)
+    X = rng.multivariate_normal(mu, P, size=50)
+    y = rng.normal(size=1)
+    eps = rng.normal(size=(50, 1))
+    assert np.allclose(enkf.diffusion_enkf(X, y, 0.4, 0.3, eps),
+                       enkf.diffusion_enkf(X, y, 0.4, 0.3, eps, mode="global"), atol=1e-12)
+
+
+def test_lagged_pcc_matches_numpy_corrcoef():
+    rng = np.random.default_rng(9)
+    a = rng.normal(size=100)
+    b = np.roll(a, 2) + 0.1 * rng.normal(size=100)
+    for lag in (0, 1, 2, 5):
+        ref = np.corrcoef(b[lag:], a[:100 - lag])[0, 1]
+        assert abs(metrics.lagged_pcc(b, a, lag) - ref) < 1e-12
+
+
+# ------------------------------------------------ FP32 against FP64 ---------
+@pytest.mark.slow
+def test_matched_fp32_statistics_agree_with_fp64(small_graph):
+    """The op-order-matched FP32 oracle and the FP64 oracle describe the same
+    dynamics: over 2 s the rate and ISI CV agree to within what two
+    trajectories of this chaotic network differ by (the rasters themselves
+    diverge after the first near-threshold crossing)."""
+    res = {}
+    for prec in (32, 64):
+        s = oracle.Sim(small_graph, synth.default_region_params(), seed=15964, precision=prec)
+        s.step(20000)
+        st, ids = s.raster()
+        res[prec] = (len(ids), metrics.isi_cv(st, ids))
+    r32, r64 = res[32][0], res[64][0]
+    assert abs(r32 - r64) / r64 < 0.03
+    assert abs(res[32][1] - res[64][1]) < 0.05
