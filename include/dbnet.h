@@ -1,0 +1,243 @@
+/*
+ * dbnet -- GB300 (sm_103a) library for the hot path of the Digital Brain:
+ * conductance leaky integrate-and-fire networks with delayed spike delivery,
+ * the regional Balloon-Windkessel BOLD readout, and the diffusion ensemble
+ * Kalman filter of hierarchical mesoscale data assimilation (HMDA).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every int-returning call returns DBNET_OK (0) or a negative
+ *     DBNET_E* code; dbnet_strerror() names it and dbnet_last_error() gives
+ *     the detail of the most recent failure on the calling thread.  After a
+ *     CUDA failure a handle is poisoned: later calls return DBNET_ESTATE.
+ *   - Ownership: input arrays are caller-owned host memory, read (copied) at
+ *     the call and never retained.  Device state is owned by the handle and
+ *     freed by the matching *_destroy.  Output arrays are caller-allocated
+ *     host memory.
+ *   - Streams: all device work is enqueued on the CUDA stream given at
+ *     create (NULL = the legacy default stream); step calls return without
+ *     waiting, read calls synchronise that stream first.
+ *   - Threads: a handle must not be used from two threads at once.
+ *   - Units: mV, ms, nF, microsiemens, nA; BOLD model constants in seconds.
+ *   - Neuron numbering: neurons are sorted by region; inside a region the
+ *     excitatory neurons come first.  Spikes of excitatory sources drive the
+ *     AMPA and NMDA channels of their targets, inhibitory ones GABA_A and
+ *     GABA_B (Extended Data Table 2, "Synapse model").
+ */
+#ifndef DBNET_H
+#define DBNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DBNET_OK 0
+#define DBNET_EINVAL (-1)      /* malformed graph, parameters or arguments */
+#define DBNET_ENOMEM (-2)      /* device or host allocation failed */
+#define DBNET_ECUDA (-3)       /* a CUDA runtime call failed */
+#define DBNET_ETIMEOUT (-4)    /* a bounded device wait gave up */
+#define DBNET_EOVERFLOW (-5)   /* fixed-point accumulation could overflow int32 */
+#define DBNET_ESTATE (-6)      /* handle poisoned by an earlier failure */
+#define DBNET_ERANGE (-7)      /* a caller buffer or a fixed capacity is too small */
+#define DBNET_EUNSUPPORTED (-8)
+
+#define DBNET_WEIGHT_F32 0
+#define DBNET_WEIGHT_BF16 1
+
+typedef struct dbnet dbnet_t;
+typedef struct dbens dbens_t;
+
+/* Network graph: CSR by source (the paper's connection table, Supplementary
+ * Table 5, transposed so that a spiking neuron finds its out-edges; push
+ * delivery, Supplementary Algorithm 2).
+ *   n_neurons        N, 1 <= N < 2^31
+ *   n_regions        R >= 1
+ *   region_offsets   [R+1] int32, 0 = offsets[0] < ... < offsets[R] = N
+ *   n_exc            [R] int32, excitatory neurons at the start of region r
+ *   row_ptr          [N+1] int64, row_ptr[0] = 0, non-decreasing
+ *   col              [E] int32 target index, 0 <= col < N
+ *   weight           [E] non-negative synaptic weight w, as float32 or as
+ *                    BF16 bit patterns (weight_dtype); stored as BF16
+ *                    (round to nearest even) on the device
+ *   delay            [E] uint8 delay in steps, 1..255; within each row the
+ *                    delays must be non-decreasing
+ * A spike of source j at step n reaches target col[e] through edge e in the
+ * accumulator consumed at step n + delay[e].  Violations give DBNET_EINVAL. */
+typedef struct {
+  int32_t n_neurons;
+  int32_t n_regions;
+  const int32_t* region_offsets;
+  const int32_t* n_exc;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const void* weight;
+  int32_t weight_dtype;
+  const uint8_t* delay;
+} dbnet_graph_t;
+
+/* Per-region neuron and synapse constants (the property table of
+ * Supplementary Table 5, one row per region).  Channels u = AMPA, NMDA,
+ * GABA_A, GABA_B.
+ *   C, gL, VL, Vth, Vreset, Tref   membrane (Methods, capacitance-voltage eq.)
+ *   Vu[u], tau_u[u], g_u[u]        reversal potential, trace decay time and
+ *                                  maximal conductance (Methods, Eq. 2)
+ *   I_ext                          constant injected current
+ *   drive_rate_hz, drive_K, w_ext  Poisson background: drive_K independent
+ *                                  sources of rate drive_rate_hz per neuron,
+ *                                  each event adding w_ext to the excitatory
+ *                                  traces (Extended Data Table 2, "Input") */
+typedef struct {
+  double C, gL, VL, Vth, Vreset, Tref;
+  double Vu[4], tau_u[4], g_u[4];
+  double I_ext, drive_rate_hz, drive_K, w_ext;
+} dbnet_region_params_t;
+
+/* Run options.
+ *   dt_ms            Euler step (Supplementary Sec. 3: 0.1 or 1 ms)
+ *   bin_ms           neural-activity bin that feeds the BOLD model; a whole
+ *                    number of steps
+ *   tr_ms            BOLD sampling period (800 ms in the paper); a whole
+ *                    number of bins
+ *   z_scale          z = z_scale * (spikes of the region in the bin) / size
+ *   bw_*             Balloon-Windkessel constants (Extended Data Table 4)
+ *   seed, net_id     Philox4x64-10 key; the drive and the initial state of
+ *                    neuron i at step n use counter (n, i/4, stream, 0)
+ *   fixed_shift      S of the fixed-point accumulators q(w) = rint(w 2^S);
+ *                    0 = automatic (16, lowered until one step's worst-case
+ *                    arrivals fit int32)
+ *   precision        32 (FP32 state; the only mode the device path runs)
+ *   raster_capacity  spikes kept for dbnet_read_spikes (0 = none)
+ *   bold_capacity    BOLD samples kept per region */
+typedef struct {
+  double dt_ms, bin_ms, tr_ms, z_scale;
+  double bw_kappa, bw_gamma, bw_tau, bw_alpha, bw_rho, bw_V0;
+  uint64_t seed, net_id;
+  int32_t fixed_shift;
+  int32_t precision;
+  int64_t raster_capacity;
+  int64_t bold_capacity;
+} dbnet_options_t;
+
+typedef struct {
+  int64_t step;              /* steps completed */
+  int64_t spikes;            /* spikes emitted */
+  int64_t events;            /* synaptic events applied to accumulators */
+  int64_t raster_len;        /* spikes recorded */
+  int64_t raster_dropped;    /* spikes not recorded for lack of capacity */
+  int64_t bold_samples;      /* BOLD samples recorded */
+  int32_t fixed_shift;       /* S in use */
+  int32_t max_delay;         /* longest delay of the graph, steps */
+  int32_t packed_edges;      /* 1 when target and delay share one 32-bit word */
+  int32_t weights_rounded;   /* 1 when some float32 weight was not a BF16 value */
+} dbnet_stats_t;
+
+/* Name of a status code (static string). */
+const char* dbnet_strerror(int code);
+
+/* Detail of the last failure on the calling thread (static per thread). */
+const char* dbnet_last_error(void);
+
+/* Fill *o with the defaults: dt 0.1 ms, bin 1 ms, TR 800 ms, z_scale 1,
+ * the standard hemodynamic constants, seed 1, net_id 0, automatic S,
+ * precision 32, no raster, 4096 BOLD samples. */
+int dbnet_options_default(dbnet_options_t* o);
+
+/* Build a network on the current CUDA device: copy the graph and parameters,
+ * validate them on the device, pack the edges (target and delay in one
+ * 32-bit word when N <= 2^24, BF16 weight), choose S and set the initial
+ * state (V uniform in [V_reset, V_th) from Philox stream 1; traces zero).
+ * params: [n_regions].  cuda_stream: a cudaStream_t or NULL.
+ * Returns DBNET_EINVAL for a malformed graph or parameter set,
+ * DBNET_EOVERFLOW when the chosen S could overflow, DBNET_ENOMEM, DBNET_ECUDA. */
+int dbnet_create(const dbnet_graph_t* graph, const dbnet_region_params_t* params,
+                 const dbnet_options_t* options, void* cuda_stream, dbnet_t** out);
+
+/* Advance by n_steps Euler steps (Supplementary Sec. 3, Eqs. 3 and 5; push
+ * delivery, Supplementary Algorithm 2; BOLD per bin, Extended Data Table 4).
+ * Enqueued on the handle's stream; returns without waiting. */
+int dbnet_step(dbnet_t* h, int64_t n_steps);
+
+/* Wait for the handle's stream. */
+int dbnet_sync(dbnet_t* h);
+
+/* Recorded spikes with t0 <= step < t1, sorted by (step, id), written to
+ * step[] and id[] (capacity cap).  *n_out = number written; DBNET_ERANGE
+ * when more than cap match (the first cap are written). */
+int dbnet_read_spikes(dbnet_t* h, int64_t t0, int64_t t1, int32_t* step, int32_t* id,
+                      int64_t cap, int64_t* n_out);
+
+/* BOLD samples y[k][r] (row-major, k-th TR), at most cap_samples rows. */
+int dbnet_read_bold(dbnet_t* h, double* y, int64_t cap_samples, int64_t* n_out);
+
+/* Hemodynamic state x[r][4] = (s, f, v, q) per region. */
+int dbnet_read_bw(dbnet_t* h, double* x);
+
+/* Neuron state: V[N], J[4][N] (channel-major), ref[N] (remaining refractory
+ * steps).  Any pointer may be NULL. */
+int dbnet_read_state(dbnet_t* h, float* V, float* J, int32_t* ref);
+
+/* Overwrite the neuron state (same layout; NULL leaves a field unchanged).
+ * ref values must lie in 0..255. */
+int dbnet_set_state(dbnet_t* h, const float* V, const float* J, const int32_t* ref);
+
+int dbnet_stats(dbnet_t* h, dbnet_stats_t* out);
+
+void dbnet_destroy(dbnet_t* h);
+
+/* ---------------------------------------------------------------------------
+ * Ensemble of networks for HMDA (Methods, "Statistical inference ... by
+ * HMDA"; Supplementary Sec. 6 and Algorithm 3).  n_members networks share one
+ * graph and differ in their per-region AMPA and GABA_A conductance scales
+ * (the hyperparameters theta, held as natural logarithms) and in their
+ * Philox key (net_id = options.net_id + member).  The analysis state of a
+ * member is, per region r, the block (theta_AMPA, theta_GABA_A, s, f, v, q, y).
+ * ------------------------------------------------------------------------ */
+#define DBENS_DIFFUSION 0 /* one observer per region, fused with weight gamma */
+#define DBENS_GLOBAL 1    /* one observer of all regions (textbook EnKF) */
+
+typedef struct {
+  double obs_var;     /* Gamma_o: observation noise variance of every BOLD signal */
+  double gamma;       /* fusion coefficient of Supplementary Algorithm 3 */
+  double rw_sigma;    /* std of the random walk of theta per analysis */
+  double theta_lo;    /* theta is kept in [theta_lo, theta_hi] */
+  double theta_hi;
+  double floor;       /* f, v, q are kept >= floor after an analysis */
+  int32_t mode;       /* DBENS_DIFFUSION or DBENS_GLOBAL */
+} dbens_enkf_t;
+
+/* base: [R] parameters before scaling; log_scale_init: [M][R][2] initial
+ * theta (AMPA, GABA_A).  Errors as dbnet_create. */
+int ens_create(const dbnet_graph_t* graph, const dbnet_region_params_t* base,
+               int32_t n_members, const double* log_scale_init,
+               const dbnet_options_t* options, const dbens_enkf_t* enkf,
+               void* cuda_stream, dbens_t** out);
+
+/* Advance every member by n_steps (one batched launch sequence). */
+int ens_step(dbens_t* h, int64_t n_steps);
+
+/* One analysis at the current time (Supplementary Algorithm 3, steps 4-7, in
+ * FP64 on the device) against y_obs[R], using each member's latest BOLD
+ * sample, then the random walk of theta and the rescaling of the members'
+ * conductances.  eps_obs [M][R] and xi_rw [M][R][2] are standard-normal draws
+ * (NULL: drawn on the device from Philox).  y_pred_mean [R] (may be NULL)
+ * receives the forecast ensemble mean of y before the analysis. */
+int ens_assimilate(dbens_t* h, const double* y_obs, const double* eps_obs,
+                   const double* xi_rw, double* y_pred_mean);
+
+/* Member states: theta [M][R][2], bw [M][R][4], y [M][R] (latest sample).
+ * Any pointer may be NULL. */
+int ens_read(dbens_t* h, double* theta, double* bw, double* y);
+
+/* Access to one member as a network view (reads only): the returned handle
+ * is owned by the ensemble and valid until ens_destroy. */
+int ens_member(dbens_t* h, int32_t member, dbnet_t** out);
+
+void ens_destroy(dbens_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBNET_H */

@@ -1,0 +1,679 @@
+// Host engine and the dbnet_* C ABI (see include/dbnet.h).
+//
+// Create: host-side checks that cost O(N + R), then the edge arrays are
+// copied to the device, validated and packed by one warp-per-row kernel
+// (target range, delay range and order, weights -> BF16, in-degrees, largest
+// weight and delay), the fixed-point scale is chosen from those, the region
+// constants are derived in FP64 and rounded to FP32 once, and the initial
+// state is drawn on the device.
+//
+// Step: (deliver, update) kernel pairs on the handle's stream, replayed from
+// a captured CUDA graph of kChunk steps; all per-step indices live in device
+// memory, so the same graph serves every chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dbnet.h"
+#include "engine.h"
+#include "host.h"
+
+namespace dbn {
+
+thread_local std::string g_last_error;
+
+// ---------------------------------------------------------------- graph ----
+std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
+  if (!g) raise(DBNET_EINVAL, "graph is NULL");
+  const int32_t N = g->n_neurons, R = g->n_regions;
+  if (N < 1 || R < 1) raise(DBNET_EINVAL, "n_neurons and n_regions must be >= 1");
+  if (!g->region_offsets || !g->n_exc || !g->row_ptr) raise(DBNET_EINVAL, "NULL graph array");
+  if (g->weight_dtype != DBNET_WEIGHT_F32 && g->weight_dtype != DBNET_WEIGHT_BF16)
+    raise(DBNET_EINVAL, "weight_dtype must be DBNET_WEIGHT_F32 or DBNET_WEIGHT_BF16");
+  if (g->region_offsets[0] != 0 || g->region_offsets[R] != N)
+    raise(DBNET_EINVAL, "region_offsets must start at 0 and end at n_neurons");
+  for (int32_t r = 0; r < R; ++r) {
+    const int32_t sz = g->region_offsets[r + 1] - g->region_offsets[r];
+    if (sz < 1) raise(DBNET_EINVAL, "region_offsets must be strictly increasing");
+    if (g->n_exc[r] < 0 || g->n_exc[r] > sz) raise(DBNET_EINVAL, "n_exc out of range");
+  }
+  if (g->row_ptr[0] != 0) raise(DBNET_EINVAL, "row_ptr[0] must be 0");
+  for (int32_t j = 0; j < N; ++j)
+    if (g->row_ptr[j + 1] < g->row_ptr[j]) raise(DBNET_EINVAL, "row_ptr must be non-decreasing");
+  const int64_t E = g->row_ptr[N];
+  if (E >= (int64_t(1) << 47)) raise(DBNET_EINVAL, "too many edges");
+  if (E > 0 && (!g->col || !g->weight || !g->delay)) raise(DBNET_EINVAL, "NULL edge array");
+
+  auto gd = std::make_shared<GraphDev>();
+  gd->N = N;
+  gd->R = R;
+  gd->E = E;
+  gd->ro_h.assign(g->region_offsets, g->region_offsets + R + 1);
+  gd->nexc_h.assign(g->n_exc, g->n_exc + R);
+  int bits = 1;
+  while (bits < 31 && ((int64_t)1 << bits) < (int64_t)N) ++bits;
+  gd->packed = bits <= 24;
+  gd->shift = gd->packed ? bits : 32;
+  gd->tmask = gd->packed ? (uint32_t)((1u << bits) - 1u) : 0xFFFFFFFFu;
+
+  gd->row_ptr.alloc(N + 1);
+  gd->ro.alloc(R + 1);
+  gd->col.alloc(std::max<int64_t>(E, 1));
+  gd->w.alloc(std::max<int64_t>(E, 1));
+  gd->delay.alloc(std::max<int64_t>(E, 1));
+  CK(cudaMemcpyAsync(gd->row_ptr.p, g->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(gd->ro.p, g->region_offsets, sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s));
+  DevBuf<float> wstage;
+  const void* w_in = gd->w.p;
+  if (E > 0) {
+    CK(cudaMemcpyAsync(gd->col.p, g->col, sizeof(int32_t) * E, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(gd->delay.p, g->delay, E, cudaMemcpyHostToDevice, s));
+    if (g->weight_dtype == DBNET_WEIGHT_BF16) {
+      CK(cudaMemcpyAsync(gd->w.p, g->weight, sizeof(uint16_t) * E, cudaMemcpyHostToDevice, s));
+    } else {
+      wstage.alloc(E);
+      CK(cudaMemcpyAsync(wstage.p, g->weight, sizeof(float) * E, cudaMemcpyHostToDevice, s));
+      w_in = wstage.p;
+    }
+  }
+  DevBuf<int32_t> indeg;
+  indeg.alloc(N);
+  DevBuf<unsigned> scal;  // wmax bits, dmax, err, kin_max
+  scal.alloc(4);
+  CK(cudaMemsetAsync(indeg.p, 0, sizeof(int32_t) * N, s));
+  CK(cudaMemsetAsync(scal.p, 0, sizeof(unsigned) * 4, s));
+  if (E > 0)
+    launch_validate_pack(N, gd->row_ptr.p, gd->col.p, w_in, g->weight_dtype, gd->w.p,
+                         gd->delay.p, gd->shift, indeg.p, scal.p + 0, scal.p + 1, scal.p + 2, s);
+  launch_max_reduce(indeg.p, N, scal.p + 3, s);
+  CK(cudaGetLastError());
+  unsigned h[4];
+  CK(cudaMemcpyAsync(h, scal.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const unsigned err = h[2];
+  if (err & kErrTarget) raise(DBNET_EINVAL, "an edge target is outside [0, n_neurons)");
+  if (err & kErrDelayRange) raise(DBNET_EINVAL, "an edge delay is 0 (delays are 1..255 steps)");
+  if (err & kErrDelayOrder) raise(DBNET_EINVAL, "delays must be non-decreasing within each row");
+  if (err & kErrWeight) raise(DBNET_EINVAL, "weights must be finite and non-negative");
+  gd->rounded = (err & kErrRounded) != 0;
+  float wmax;
+  std::memcpy(&wmax, &h[0], 4);
+  gd->w_max = (double)wmax;
+  gd->max_delay = (int32_t)std::max(1u, h[1]);
+  gd->kin_max = (int32_t)h[3];
+  if (gd->packed) gd->delay.reset();
+  return gd;
+}
+
+// ---------------------------------------------------- region constants ----
+static bool finite(double x) { return std::isfinite(x); }
+
+void check_params(const dbnet_region_params_t& p, double dt) {
+  if (!(p.C > 0) || !finite(p.C)) raise(DBNET_EINVAL, "C must be > 0");
+  if (!(p.gL >= 0) || !finite(p.gL)) raise(DBNET_EINVAL, "gL must be >= 0");
+  for (double v : {p.VL, p.Vth, p.Vreset, p.I_ext})
+    if (!finite(v)) raise(DBNET_EINVAL, "non-finite membrane constant");
+  if (!(p.Tref >= 0) || std::lrint(p.Tref / dt) > 255) raise(DBNET_EINVAL, "Tref must be in [0, 255 dt]");
+  for (int u = 0; u < 4; ++u) {
+    if (!(p.tau_u[u] > 0)) raise(DBNET_EINVAL, "tau_u must be > 0");
+    if (!finite(p.g_u[u]) || !finite(p.Vu[u])) raise(DBNET_EINVAL, "non-finite synapse constant");
+  }
+  if (!(p.drive_rate_hz >= 0) || !(p.drive_K >= 0) || !(p.w_ext >= 0) || !finite(p.w_ext) ||
+      !finite(p.drive_rate_hz * p.drive_K))
+    raise(DBNET_EINVAL, "drive constants must be finite and >= 0");
+}
+
+// Thresholds of the integer-inversion Poisson draw: floor(P(X <= k) 2^32) for
+// the leading k (at most 16) whose value stays below 2^32.
+int poisson_thresholds(double lam, uint32_t* thr) {
+  double p = std::exp(-lam);
+  double cdf = p;
+  int n = 0;
+  for (int k = 0; k < kMaxThr; ++k) {
+    const double t = std::floor(std::ldexp(cdf, 32));
+    if (t >= 4294967296.0) break;
+    thr[k] = (uint32_t)t;
+    n = k + 1;
+    p = p * lam;
+    p = p / (double)(k + 1);
+    cdf = cdf + p;
+  }
+  return n;
+}
+
+RegionConst region_const(const dbnet_region_params_t& p, double dt, int S, int32_t start,
+                         int32_t end, int32_t exc_end) {
+  RegionConst c;
+  std::memset(&c, 0, sizeof(c));
+  c.dtC = (float)(dt / p.C);
+  c.gL = (float)p.gL;
+  c.VL = (float)p.VL;
+  c.Vth = (float)p.Vth;
+  c.Vreset = (float)p.Vreset;
+  c.Iext = (float)p.I_ext;
+  for (int u = 0; u < 4; ++u) {
+    c.g[u] = (float)p.g_u[u];
+    c.Vu[u] = (float)p.Vu[u];
+    c.dec[u] = (float)std::exp(-dt / p.tau_u[u]);
+  }
+  c.n_ref = (int32_t)std::lrint(p.Tref / dt);
+  c.q_ext = (int32_t)std::lrint(std::ldexp(p.w_ext, S));
+  c.n_thr = poisson_thresholds(p.drive_K * p.drive_rate_hz * dt * 1e-3, c.thr);
+  c.start = start;
+  c.end = end;
+  c.exc_end = exc_end;
+  return c;
+}
+
+int choose_shift(const GraphDev& g, double wext_max, int32_t requested) {
+  auto bound = [&](int S) {
+    return (double)g.kin_max * std::rint(std::ldexp(g.w_max, S)) +
+           16.0 * std::rint(std::ldexp(wext_max, S));
+  };
+  if (requested < 0 || requested > 30) raise(DBNET_EINVAL, "fixed_shift must be in 0..30");
+  int S = requested > 0 ? requested : 16;
+  if (requested == 0)
+    while (S > 0 && bound(S) > 2147483647.0) --S;
+  if (bound(S) > 2147483647.0)
+    raise(DBNET_EOVERFLOW, "one step's worst-case arrivals overflow int32 at this fixed_shift");
+  return S;
+}
+
+void check_options(const dbnet_options_t& o) {
+  if (!(o.dt_ms > 0) || !finite(o.dt_ms)) raise(DBNET_EINVAL, "dt_ms must be > 0");
+  const double spb = o.bin_ms / o.dt_ms;
+  if (!(spb >= 0.5) || std::fabs(spb - std::rint(spb)) > 1e-6 * spb)
+    raise(DBNET_EINVAL, "bin_ms must be a whole number of steps");
+  const double bpt = o.tr_ms / o.bin_ms;
+  if (!(bpt >= 0.5) || std::fabs(bpt - std::rint(bpt)) > 1e-6 * bpt)
+    raise(DBNET_EINVAL, "tr_ms must be a whole number of bins");
+  if (o.precision != 32) raise(DBNET_EUNSUPPORTED, "the device path computes FP32 state (precision 32)");
+  if (o.raster_capacity < 0 || o.bold_capacity < 0) raise(DBNET_EINVAL, "negative capacity");
+  if (!(o.bw_alpha > 0) || !(o.bw_tau > 0) || !(o.bw_rho > 0 && o.bw_rho < 1))
+    raise(DBNET_EINVAL, "Balloon-Windkessel constants out of range");
+  if (!finite(o.z_scale)) raise(DBNET_EINVAL, "z_scale must be finite");
+  if (o.fixed_shift < 0 || o.fixed_shift > 30) raise(DBNET_EINVAL, "fixed_shift must be in 0..30");
+}
+
+// --------------------------------------------------------------- engine ----
+void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
+  if (user_stream) {
+    stream = (cudaStream_t)user_stream;
+    own_stream = false;
+  } else {
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  const int n = (int)specs.size();
+  inst.resize(n);
+  // fixed-point scale shared by the engine
+  double wext_max = 0.0;
+  for (const auto& sp : specs)
+    for (const auto& p : sp.params) wext_max = std::max(wext_max, p.w_ext);
+  int S = 16;
+  for (int k = 0; k < n; ++k) S = std::min(S, choose_shift(*specs[k].graph, wext_max, specs[0].opt.fixed_shift));
+  shift_S = S;
+  // layout
+  int64_t tiles = 0;
+  int32_t rbase = 0;
+  uint64_t list_cap = 0;
+  for (int k = 0; k < n; ++k) {
+    const InstSpec& sp = specs[k];
+    InstHost& ih = inst[k];
+    const GraphDev& g = *sp.graph;
+    ih.graph = sp.graph;
+    ih.first_tile = (int32_t)tiles;
+    ih.n_tiles = (g.N + kTile - 1) / kTile;
+    tiles += ih.n_tiles;
+    ih.rbase = rbase;
+    rbase += g.R;
+    int min_nref = 255;
+    for (int32_t r = 0; r < g.R; ++r) {
+      ih.rc_h.push_back(region_const(sp.params[r], sp.opt.dt_ms, S, g.ro_h[r], g.ro_h[r + 1],
+                                     g.ro_h[r] + g.nexc_h[r]));
+      min_nref = std::min(min_nref, (int)ih.rc_h.back().n_ref);
+    }
+    const uint64_t per = (uint64_t)((g.max_delay + min_nref) / (min_nref + 1));
+    list_cap += (uint64_t)g.N * std::max<uint64_t>(per, 1);
+    ih.opt = sp.opt;
+    ih.net_id = sp.net_id;
+  }
+  list_cap = std::min<uint64_t>(std::max<uint64_t>(list_cap, 1024), uint64_t(1) << 28);
+  n_tiles = (int32_t)tiles;
+  total_R = rbase;
+  stride = tiles * kTile;
+
+  V.alloc(stride);
+  J.alloc(4 * stride);
+  ref.alloc(stride);
+  acc.alloc(stride);
+  CK(cudaMemsetAsync(V.p, 0, sizeof(float) * stride, stream));
+  CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
+  CK(cudaMemsetAsync(ref.p, 0, stride, stream));
+  CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * stride, stream));
+  std::vector<int32_t> tile_inst_h((size_t)tiles), region_inst_h((size_t)total_R);
+  std::vector<InstDesc> desc_h((size_t)n);
+  for (int k = 0; k < n; ++k) {
+    InstHost& ih = inst[k];
+    const GraphDev& g = *ih.graph;
+    for (int t = 0; t < ih.n_tiles; ++t) tile_inst_h[(size_t)(ih.first_tile + t)] = k;
+    for (int32_t r = 0; r < g.R; ++r) region_inst_h[(size_t)(ih.rbase + r)] = k;
+    ih.rc.alloc(g.R);
+    CK(cudaMemcpyAsync(ih.rc.p, ih.rc_h.data(), sizeof(RegionConst) * g.R, cudaMemcpyHostToDevice, stream));
+    const dbnet_options_t& o = ih.opt;
+    ih.bold.alloc(std::max<int64_t>(o.bold_capacity, 1) * g.R);
+    if (o.raster_capacity > 0) {
+      ih.raster_step.alloc(o.raster_capacity);
+      ih.raster_id.alloc(o.raster_capacity);
+    }
+    InstDesc& d = desc_h[(size_t)k];
+    std::memset(&d, 0, sizeof(d));
+    d.row_ptr = g.row_ptr.p;
+    d.col = g.col.p;
+    d.w = g.w.p;
+    d.delay = g.packed ? nullptr : g.delay.p;
+    d.region_offsets = g.ro.p;
+    d.rc = ih.rc.p;
+    d.bold = ih.bold.p;
+    d.raster_step = ih.raster_step.p;
+    d.raster_id = ih.raster_id.p;
+    d.base = (int64_t)ih.first_tile * kTile;
+    d.raster_cap = o.raster_capacity;
+    d.bold_cap = o.bold_capacity;
+    d.seed = o.seed;
+    d.net_id = ih.net_id;
+    d.N = g.N;
+    d.R = g.R;
+    d.rbase = ih.rbase;
+    d.shift = g.shift;
+    d.tmask = g.tmask;
+    d.two_S = std::ldexp(1.0f, S);
+    d.inv_two_S = std::ldexp(1.0f, -S);
+    d.spb = (int32_t)std::lrint(o.bin_ms / o.dt_ms);
+    d.bins_per_tr = (int32_t)std::lrint(o.tr_ms / o.bin_ms);
+    d.h_bw = o.bin_ms * 1e-3;
+    d.z_scale = o.z_scale;
+    d.kappa = o.bw_kappa;
+    d.gamma = o.bw_gamma;
+    d.tau = o.bw_tau;
+    d.alpha = o.bw_alpha;
+    d.rho = o.bw_rho;
+    d.V0 = o.bw_V0;
+    ih.desc = d;
+  }
+  desc.alloc(n);
+  dyn.alloc(n);
+  tile_inst.alloc(std::max<int64_t>(tiles, 1));
+  region_inst.alloc(std::max(total_R, 1));
+  cnt.alloc(std::max(total_R, 1));
+  bw.alloc(4 * std::max(total_R, 1));
+  ylast.alloc(std::max(total_R, 1));
+  list0.alloc(list_cap);
+  list1.alloc(list_cap);
+  count.alloc(2);
+  iter.alloc(1);
+  done.alloc(1);
+  events.alloc(1);
+  flags.alloc(1);
+  std::vector<InstDyn> dyn_h((size_t)n);
+  std::memset(dyn_h.data(), 0, sizeof(InstDyn) * n);
+  for (auto& x : dyn_h) x.active = 1;
+  std::vector<double> bw_h((size_t)total_R * 4);
+  for (int32_t r = 0; r < total_R; ++r) {
+    bw_h[(size_t)r * 4 + 0] = 0.0;
+    bw_h[(size_t)r * 4 + 1] = 1.0;
+    bw_h[(size_t)r * 4 + 2] = 1.0;
+    bw_h[(size_t)r * 4 + 3] = 1.0;
+  }
+  CK(cudaMemcpyAsync(desc.p, desc_h.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(dyn.p, dyn_h.data(), sizeof(InstDyn) * n, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(tile_inst.p, tile_inst_h.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(region_inst.p, region_inst_h.data(), sizeof(int32_t) * total_R, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(total_R, 1), stream));
+  CK(cudaMemcpyAsync(bw.p, bw_h.data(), sizeof(double) * 4 * total_R, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(ylast.p, 0, sizeof(double) * std::max(total_R, 1), stream));
+  CK(cudaMemsetAsync(count.p, 0, sizeof(uint32_t) * 2, stream));
+  CK(cudaMemsetAsync(iter.p, 0, sizeof(unsigned long long), stream));
+  CK(cudaMemsetAsync(done.p, 0, sizeof(unsigned), stream));
+  CK(cudaMemsetAsync(events.p, 0, sizeof(unsigned long long), stream));
+  CK(cudaMemsetAsync(flags.p, 0, sizeof(unsigned), stream));
+
+  dev = EngineDev{};
+  dev.V = V.p;
+  dev.J = J.p;
+  dev.ref = ref.p;
+  dev.acc = acc.p;
+  dev.stride = stride;
+  dev.insts = desc.p;
+  dev.dyn = dyn.p;
+  dev.tile_inst = tile_inst.p;
+  dev.cnt = cnt.p;
+  dev.bw = bw.p;
+  dev.ylast = ylast.p;
+  dev.region_inst = region_inst.p;
+  dev.list0 = list0.p;
+  dev.list1 = list1.p;
+  dev.count = count.p;
+  dev.iter = iter.p;
+  dev.done = done.p;
+  dev.events = events.p;
+  dev.flags = flags.p;
+  dev.list_cap = list_cap;
+  dev.n_inst = n;
+  dev.n_tiles = n_tiles;
+  dev.total_R = total_R;
+  for (int k = 0; k < n; ++k) launch_init_state(dev, k, inst[k].n_tiles, inst[k].first_tile, stream);
+  del_grid = deliver_grid();
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(stream));
+}
+
+Engine::~Engine() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (own_stream && stream) {
+    cudaStreamSynchronize(stream);
+    cudaStreamDestroy(stream);
+  } else if (stream) {
+    cudaStreamSynchronize(stream);
+  }
+}
+
+void Engine::check() const {
+  if (poisoned) raise(DBNET_ESTATE, "handle poisoned by an earlier failure: " + poison_msg);
+}
+
+void Engine::capture() {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < kChunk; ++i) {
+    launch_deliver(dev, del_grid, stream);
+    launch_update(dev, stream);
+  }
+  cudaError_t e1 = cudaStreamEndCapture(stream, &g);
+  if (e1 != cudaSuccess) raise(DBNET_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+  cudaError_t e2 = cudaGraphInstantiate(&gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) raise(DBNET_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+}
+
+void Engine::step(int64_t n) {
+  check();
+  if (n < 0) raise(DBNET_EINVAL, "n_steps must be >= 0");
+  if (n >= kChunk && !gexec) capture();
+  while (n >= kChunk) {
+    CK(cudaGraphLaunch(gexec, stream));
+    n -= kChunk;
+  }
+  for (; n > 0; --n) {
+    launch_deliver(dev, del_grid, stream);
+    launch_update(dev, stream);
+  }
+  CK(cudaGetLastError());
+}
+
+void Engine::sync() {
+  check();
+  CK(cudaStreamSynchronize(stream));
+  unsigned f = 0;
+  CK(cudaMemcpy(&f, flags.p, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f & kFlagListOverflow)
+    raise(DBNET_ERANGE, "live delivery list overflowed its capacity");
+}
+
+InstDyn Engine::read_dyn(int k) {
+  sync();
+  InstDyn d;
+  CK(cudaMemcpy(&d, dyn.p + k, sizeof(d), cudaMemcpyDeviceToHost));
+  return d;
+}
+
+}  // namespace dbn
+
+// ------------------------------------------------------------------ ABI ----
+using namespace dbn;
+
+struct dbnet {
+  std::unique_ptr<Engine> own;  // null for a member view of an ensemble
+  Engine* eng = nullptr;
+  int inst = 0;
+};
+
+template <class F>
+static int guarded(Engine* eng, F&& f) {
+  try {
+    f();
+    return DBNET_OK;
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    if (eng && e.code == DBNET_ECUDA) {
+      eng->poisoned = true;
+      eng->poison_msg = e.msg;
+    }
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return DBNET_ENOMEM;
+  } catch (...) {
+    g_last_error = "unexpected failure";
+    return DBNET_ECUDA;
+  }
+}
+
+extern "C" {
+
+const char* dbnet_strerror(int code) {
+  switch (code) {
+    case DBNET_OK: return "ok";
+    case DBNET_EINVAL: return "invalid argument";
+    case DBNET_ENOMEM: return "out of memory";
+    case DBNET_ECUDA: return "CUDA failure";
+    case DBNET_ETIMEOUT: return "device wait timed out";
+    case DBNET_EOVERFLOW: return "fixed-point accumulation could overflow";
+    case DBNET_ESTATE: return "handle poisoned by an earlier failure";
+    case DBNET_ERANGE: return "capacity exceeded";
+    case DBNET_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* dbnet_last_error(void) { return g_last_error.c_str(); }
+
+int dbnet_options_default(dbnet_options_t* o) {
+  if (!o) return DBNET_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->dt_ms = 0.1;
+  o->bin_ms = 1.0;
+  o->tr_ms = 800.0;
+  o->z_scale = 1.0;
+  o->bw_kappa = 0.65;
+  o->bw_gamma = 0.41;
+  o->bw_tau = 0.98;
+  o->bw_alpha = 0.32;
+  o->bw_rho = 0.34;
+  o->bw_V0 = 0.02;
+  o->seed = 1;
+  o->net_id = 0;
+  o->fixed_shift = 0;
+  o->precision = 32;
+  o->raster_capacity = 0;
+  o->bold_capacity = 4096;
+  return DBNET_OK;
+}
+
+int dbnet_create(const dbnet_graph_t* graph, const dbnet_region_params_t* params,
+                 const dbnet_options_t* options, void* cuda_stream, dbnet_t** out) {
+  if (out) *out = nullptr;
+  std::unique_ptr<dbnet> h(new (std::nothrow) dbnet());
+  if (!h) return DBNET_ENOMEM;
+  int rc = guarded(nullptr, [&] {
+    if (!out || !params || !options) raise(DBNET_EINVAL, "NULL argument");
+    check_options(*options);
+    if (!graph) raise(DBNET_EINVAL, "graph is NULL");
+    if (graph->n_regions < 1) raise(DBNET_EINVAL, "n_regions must be >= 1");
+    for (int32_t r = 0; r < graph->n_regions; ++r) check_params(params[r], options->dt_ms);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    auto g = upload_graph(graph, s);
+    InstSpec sp;
+    sp.graph = g;
+    sp.params.assign(params, params + graph->n_regions);
+    sp.opt = *options;
+    sp.net_id = options->net_id;
+    h->own.reset(new Engine());
+    h->eng = h->own.get();
+    h->eng->init({sp}, cuda_stream);
+  });
+  if (rc == DBNET_OK) *out = h.release();
+  return rc;
+}
+
+int dbnet_step(dbnet_t* h, int64_t n_steps) {
+  if (!h || !h->own) return DBNET_EINVAL;
+  return guarded(h->eng, [&] { h->eng->step(n_steps); });
+}
+
+int dbnet_sync(dbnet_t* h) {
+  if (!h) return DBNET_EINVAL;
+  return guarded(h->eng, [&] { h->eng->sync(); });
+}
+
+int dbnet_read_spikes(dbnet_t* h, int64_t t0, int64_t t1, int32_t* step, int32_t* id, int64_t cap,
+                      int64_t* n_out) {
+  if (!h || !n_out || cap < 0 || (cap > 0 && (!step || !id))) return DBNET_EINVAL;
+  *n_out = 0;
+  int64_t matched = 0;
+  int rc = guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    const InstHost& ih = e.inst[h->inst];
+    InstDyn d = e.read_dyn(h->inst);
+    const int64_t n = std::min<int64_t>((int64_t)d.raster_count, ih.opt.raster_capacity);
+    std::vector<int32_t> s((size_t)n), i((size_t)n);
+    if (n > 0) {
+      CK(cudaMemcpy(s.data(), ih.raster_step.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(i.data(), ih.raster_id.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    }
+    std::vector<uint64_t> key;
+    key.reserve((size_t)n);
+    for (int64_t k = 0; k < n; ++k)
+      if (s[(size_t)k] >= t0 && s[(size_t)k] < t1)
+        key.push_back(((uint64_t)(uint32_t)s[(size_t)k] << 32) | (uint32_t)i[(size_t)k]);
+    std::sort(key.begin(), key.end());
+    matched = (int64_t)key.size();
+    const int64_t w = std::min<int64_t>(matched, cap);
+    for (int64_t k = 0; k < w; ++k) {
+      step[k] = (int32_t)(key[(size_t)k] >> 32);
+      id[k] = (int32_t)(key[(size_t)k] & 0xFFFFFFFFu);
+    }
+    *n_out = w;
+  });
+  if (rc == DBNET_OK && matched > cap) {
+    g_last_error = "more spikes match than cap";
+    return DBNET_ERANGE;
+  }
+  return rc;
+}
+
+int dbnet_read_bold(dbnet_t* h, double* y, int64_t cap_samples, int64_t* n_out) {
+  if (!h || !n_out || cap_samples < 0 || (cap_samples > 0 && !y)) return DBNET_EINVAL;
+  *n_out = 0;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    const InstHost& ih = e.inst[h->inst];
+    InstDyn d = e.read_dyn(h->inst);
+    const int64_t avail = std::min<int64_t>(d.bold_count, ih.opt.bold_capacity);
+    const int64_t n = std::min(avail, cap_samples);
+    if (n > 0)
+      CK(cudaMemcpy(y, ih.bold.p, sizeof(double) * n * ih.graph->R, cudaMemcpyDeviceToHost));
+    *n_out = n;
+  });
+}
+
+int dbnet_read_bw(dbnet_t* h, double* x) {
+  if (!h || !x) return DBNET_EINVAL;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    e.sync();
+    const InstHost& ih = e.inst[h->inst];
+    CK(cudaMemcpy(x, e.bw.p + 4 * ih.rbase, sizeof(double) * 4 * ih.graph->R, cudaMemcpyDeviceToHost));
+  });
+}
+
+int dbnet_read_state(dbnet_t* h, float* V, float* J, int32_t* ref) {
+  if (!h) return DBNET_EINVAL;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    e.sync();
+    const InstHost& ih = e.inst[h->inst];
+    const int64_t base = (int64_t)ih.first_tile * kTile;
+    const int32_t N = ih.graph->N;
+    if (V) CK(cudaMemcpy(V, e.V.p + base, sizeof(float) * N, cudaMemcpyDeviceToHost));
+    if (J)
+      for (int u = 0; u < 4; ++u)
+        CK(cudaMemcpy(J + (int64_t)u * N, e.J.p + u * e.stride + base, sizeof(float) * N,
+                      cudaMemcpyDeviceToHost));
+    if (ref) {
+      std::vector<uint8_t> r((size_t)N);
+      CK(cudaMemcpy(r.data(), e.ref.p + base, N, cudaMemcpyDeviceToHost));
+      for (int32_t i = 0; i < N; ++i) ref[i] = r[(size_t)i];
+    }
+  });
+}
+
+int dbnet_set_state(dbnet_t* h, const float* V, const float* J, const int32_t* ref) {
+  if (!h || !h->own) return DBNET_EINVAL;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    e.sync();
+    const InstHost& ih = e.inst[h->inst];
+    const int64_t base = (int64_t)ih.first_tile * kTile;
+    const int32_t N = ih.graph->N;
+    std::vector<uint8_t> r;
+    if (ref) {
+      r.resize((size_t)N);
+      for (int32_t i = 0; i < N; ++i) {
+        if (ref[i] < 0 || ref[i] > 255) raise(DBNET_EINVAL, "ref values must be in 0..255");
+        r[(size_t)i] = (uint8_t)ref[i];
+      }
+    }
+    if (V) CK(cudaMemcpy(e.V.p + base, V, sizeof(float) * N, cudaMemcpyHostToDevice));
+    if (J)
+      for (int u = 0; u < 4; ++u)
+        CK(cudaMemcpy(e.J.p + u * e.stride + base, J + (int64_t)u * N, sizeof(float) * N,
+                      cudaMemcpyHostToDevice));
+    if (ref) CK(cudaMemcpy(e.ref.p + base, r.data(), N, cudaMemcpyHostToDevice));
+  });
+}
+
+int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
+  if (!h || !out) return DBNET_EINVAL;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    const InstHost& ih = e.inst[h->inst];
+    InstDyn d = e.read_dyn(h->inst);
+    unsigned long long ev = 0;
+    CK(cudaMemcpy(&ev, e.events.p, sizeof(ev), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    out->step = d.step;
+    out->spikes = (int64_t)d.spikes;
+    out->events = (int64_t)ev;
+    const int64_t cap = ih.opt.raster_capacity;
+    out->raster_len = std::min<int64_t>((int64_t)d.raster_count, cap);
+    out->raster_dropped = std::max<int64_t>((int64_t)d.raster_count - cap, 0);
+    out->bold_samples = std::min<int64_t>(d.bold_count, ih.opt.bold_capacity);
+    out->fixed_shift = e.shift_S;
+    out->max_delay = ih.graph->max_delay;
+    out->packed_edges = ih.graph->packed ? 1 : 0;
+    out->weights_rounded = ih.graph->rounded ? 1 : 0;
+  });
+}
+
+void dbnet_destroy(dbnet_t* h) {
+  if (!h || !h->own) return;  // member views belong to their ensemble
+  delete h;
+}
+
+}  // extern "C"

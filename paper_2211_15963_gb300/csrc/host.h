@@ -1,0 +1,144 @@
+// Host-side engine types shared by engine.cu and ens.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dbnet.h"
+#include "engine.h"
+
+namespace dbn {
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] inline void raise(int code, const std::string& msg) { throw Error{code, msg}; }
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t _e = (call);                                                          \
+    if (_e != cudaSuccess)                                                            \
+      ::dbn::raise(_e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,      \
+                   std::string(#call) + ": " + cudaGetErrorString(_e));               \
+  } while (0)
+
+extern thread_local std::string g_last_error;
+
+// Device allocation owned by its holder.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  int64_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { reset(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { reset(); }
+  void alloc(int64_t count) {
+    reset();
+    if (count <= 0) return;
+    cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      raise(e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,
+            "cudaMalloc of " + std::to_string(sizeof(T) * (size_t)count) + " bytes: " +
+                cudaGetErrorString(e));
+    }
+    n = count;
+  }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct GraphDev {
+  int32_t N = 0, R = 0;
+  int64_t E = 0;
+  std::vector<int32_t> ro_h, nexc_h;
+  DevBuf<int64_t> row_ptr;
+  DevBuf<uint32_t> col;
+  DevBuf<uint16_t> w;
+  DevBuf<uint8_t> delay;
+  DevBuf<int32_t> ro;
+  int32_t shift = 32;
+  uint32_t tmask = 0xFFFFFFFFu;
+  bool packed = false;
+  bool rounded = false;
+  int32_t max_delay = 1, kin_max = 0;
+  double w_max = 0.0;
+};
+
+struct InstSpec {
+  std::shared_ptr<GraphDev> graph;
+  std::vector<dbnet_region_params_t> params;  // [R]
+  dbnet_options_t opt;
+  uint64_t net_id = 0;
+};
+
+struct InstHost {
+  std::shared_ptr<GraphDev> graph;
+  std::vector<RegionConst> rc_h;
+  DevBuf<RegionConst> rc;
+  DevBuf<double> bold;
+  DevBuf<int32_t> raster_step, raster_id;
+  InstDesc desc;
+  dbnet_options_t opt;
+  uint64_t net_id = 0;
+  int32_t first_tile = 0, n_tiles = 0, rbase = 0;
+};
+
+struct Engine {
+  static constexpr int kChunk = 64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<InstHost> inst;
+  DevBuf<float> V, J;
+  DevBuf<uint8_t> ref;
+  DevBuf<int2> acc;
+  DevBuf<InstDesc> desc;
+  DevBuf<InstDyn> dyn;
+  DevBuf<int32_t> tile_inst, region_inst, cnt;
+  DevBuf<double> bw, ylast;
+  DevBuf<Entry> list0, list1;
+  DevBuf<uint32_t> count;
+  DevBuf<unsigned long long> iter, events;
+  DevBuf<unsigned> done, flags;
+  EngineDev dev{};
+  cudaGraphExec_t gexec = nullptr;
+  int del_grid = 0;
+  int32_t n_tiles = 0, total_R = 0, shift_S = 16;
+  int64_t stride = 0;
+  bool poisoned = false;
+  std::string poison_msg;
+
+  Engine() = default;
+  Engine(const Engine&) = delete;
+  ~Engine();
+  void init(const std::vector<InstSpec>& specs, void* user_stream);
+  void check() const;
+  void capture();
+  void step(int64_t n);
+  void sync();
+  InstDyn read_dyn(int k);
+};
+
+std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s);
+void check_params(const dbnet_region_params_t& p, double dt);
+void check_options(const dbnet_options_t& o);
+RegionConst region_const(const dbnet_region_params_t& p, double dt, int S, int32_t start,
+                         int32_t end, int32_t exc_end);
+
+}  // namespace dbn

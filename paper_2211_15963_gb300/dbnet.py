@@ -1,0 +1,332 @@
+"""ctypes binding of include/dbnet.h.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library (libdbnet.so, built in place by ``_build.build``).  The functions
+carry the C names; ``Network`` and ``Ensemble`` are small owners of a handle.
+Host arrays may be numpy arrays or CPU torch tensors (pinned ones included);
+a CUDA stream may be given as a ``torch.cuda.Stream``, an integer handle or
+None (the library then uses a stream of its own).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libdbnet.so")
+_lock = threading.Lock()
+_lib = None
+
+DBNET_OK = 0
+DBNET_EINVAL = -1
+DBNET_ENOMEM = -2
+DBNET_ECUDA = -3
+DBNET_ETIMEOUT = -4
+DBNET_EOVERFLOW = -5
+DBNET_ESTATE = -6
+DBNET_ERANGE = -7
+DBNET_EUNSUPPORTED = -8
+DBNET_WEIGHT_F32 = 0
+DBNET_WEIGHT_BF16 = 1
+DBENS_DIFFUSION = 0
+DBENS_GLOBAL = 1
+
+_d, _i32, _i64, _u64, _vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+
+
+class dbnet_graph_t(ctypes.Structure):
+    _fields_ = [("n_neurons", _i32), ("n_regions", _i32), ("region_offsets", _vp),
+                ("n_exc", _vp), ("row_ptr", _vp), ("col", _vp), ("weight", _vp),
+                ("weight_dtype", _i32), ("delay", _vp)]
+
+
+class dbnet_region_params_t(ctypes.Structure):
+    _fields_ = [("C", _d), ("gL", _d), ("VL", _d), ("Vth", _d), ("Vreset", _d), ("Tref", _d),
+                ("Vu", _d * 4), ("tau_u", _d * 4), ("g_u", _d * 4), ("I_ext", _d),
+                ("drive_rate_hz", _d), ("drive_K", _d), ("w_ext", _d)]
+
+
+class dbnet_options_t(ctypes.Structure):
+    _fields_ = [("dt_ms", _d), ("bin_ms", _d), ("tr_ms", _d), ("z_scale", _d),
+                ("bw_kappa", _d), ("bw_gamma", _d), ("bw_tau", _d), ("bw_alpha", _d),
+                ("bw_rho", _d), ("bw_V0", _d), ("seed", _u64), ("net_id", _u64),
+                ("fixed_shift", _i32), ("precision", _i32), ("raster_capacity", _i64),
+                ("bold_capacity", _i64)]
+
+
+class dbnet_stats_t(ctypes.Structure):
+    _fields_ = [("step", _i64), ("spikes", _i64), ("events", _i64), ("raster_len", _i64),
+                ("raster_dropped", _i64), ("bold_samples", _i64), ("fixed_shift", _i32),
+                ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32)]
+
+
+class dbens_enkf_t(ctypes.Structure):
+    _fields_ = [("obs_var", _d), ("gamma", _d), ("rw_sigma", _d), ("theta_lo", _d),
+                ("theta_hi", _d), ("floor", _d), ("mode", _i32)]
+
+
+_SIGS = {
+    "dbnet_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "dbnet_last_error": (ctypes.c_char_p, []),
+    "dbnet_options_default": (ctypes.c_int, [ctypes.POINTER(dbnet_options_t)]),
+    "dbnet_create": (ctypes.c_int, [ctypes.POINTER(dbnet_graph_t), _vp,
+                                    ctypes.POINTER(dbnet_options_t), _vp, ctypes.POINTER(_vp)]),
+    "dbnet_step": (ctypes.c_int, [_vp, _i64]),
+    "dbnet_sync": (ctypes.c_int, [_vp]),
+    "dbnet_read_spikes": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "dbnet_read_bold": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "dbnet_read_bw": (ctypes.c_int, [_vp, _vp]),
+    "dbnet_read_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "dbnet_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "dbnet_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dbnet_stats_t)]),
+    "dbnet_destroy": (None, [_vp]),
+    "ens_create": (ctypes.c_int, [ctypes.POINTER(dbnet_graph_t), _vp, _i32, _vp,
+                                  ctypes.POINTER(dbnet_options_t), ctypes.POINTER(dbens_enkf_t),
+                                  _vp, ctypes.POINTER(_vp)]),
+    "ens_step": (ctypes.c_int, [_vp, _i64]),
+    "ens_assimilate": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ens_read": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "ens_member": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp)]),
+    "ens_destroy": (None, [_vp]),
+}
+
+
+def library_path() -> str:
+    return _SO
+
+
+def lib():
+    """Load the in-tree CUDA library; fail loudly when it was not built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_SO):
+                raise RuntimeError("libdbnet.so is not built: run __graft_entry__.build() "
+                                   "(nvcc for sm_103a); there is no CPU fallback")
+            L = ctypes.CDLL(_SO)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class DbnetError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        L = lib()
+        self.code = code
+        msg = "%s: %s (%s)" % (where, L.dbnet_strerror(code).decode(),
+                               L.dbnet_last_error().decode())
+        super().__init__(msg)
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != DBNET_OK:
+        raise DbnetError(rc, where)
+
+
+def _addr(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            raise ValueError("graph arrays are host memory")
+        return int(a.data_ptr())
+    raise TypeError("expected a numpy array or a CPU tensor")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+# ------------------------------------------------------------ structures ----
+def dbnet_options_default(**over) -> dbnet_options_t:
+    o = dbnet_options_t()
+    _check(lib().dbnet_options_default(ctypes.byref(o)), "dbnet_options_default")
+    for k, v in over.items():
+        if k.startswith("bw") and isinstance(v, dict):
+            continue
+        setattr(o, k, v)
+    return o
+
+
+def options_from(opts) -> dbnet_options_t:
+    if isinstance(opts, dbnet_options_t):
+        return opts
+    opts = dict(opts or {})
+    bw = opts.pop("bw", None)
+    o = dbnet_options_default(**opts)
+    if bw:
+        for k, v in bw.items():
+            setattr(o, "bw_" + k, float(v))
+    return o
+
+
+def region_params(p: dict) -> dbnet_region_params_t:
+    r = dbnet_region_params_t()
+    for k in ("C", "gL", "VL", "Vth", "Vreset", "Tref", "I_ext", "drive_rate_hz", "drive_K", "w_ext"):
+        setattr(r, k, float(p[k]))
+    for k in ("Vu", "tau_u", "g_u"):
+        arr = getattr(r, k)
+        for u in range(4):
+            arr[u] = float(p[k][u])
+    return r
+
+
+def params_array(params, n_regions: int):
+    if isinstance(params, dict):
+        params = [params] * n_regions
+    if len(params) != n_regions:
+        raise ValueError("one parameter set per region is needed")
+    return (dbnet_region_params_t * n_regions)(*[region_params(p) for p in params])
+
+
+def graph_struct(graph):
+    """dbnet_graph_t over the arrays of a graph object with fields n_neurons,
+    n_regions, region_offsets, n_exc, row_ptr, col, w_bf16 (or weight) and
+    delay.  Returns (struct, keepalive)."""
+    ro = np.ascontiguousarray(graph.region_offsets, dtype=np.int32)
+    ne = np.ascontiguousarray(graph.n_exc, dtype=np.int32)
+    rp = graph.row_ptr
+    if isinstance(rp, np.ndarray):
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+    w = getattr(graph, "w_bf16", None)
+    dtype = DBNET_WEIGHT_BF16
+    if w is None:
+        w = graph.weight
+        dtype = DBNET_WEIGHT_F32
+    g = dbnet_graph_t(int(graph.n_neurons), int(graph.n_regions), _addr(ro), _addr(ne), _addr(rp),
+                      _addr(graph.col), _addr(w), dtype, _addr(graph.delay))
+    return g, (ro, ne, rp, graph)
+
+
+# --------------------------------------------------------------- network ----
+def dbnet_create(graph, params, options=None, stream=None) -> ctypes.c_void_p:
+    g, keep = graph_struct(graph)
+    P = params_array(params, int(graph.n_regions))
+    o = options_from(options)
+    h = _vp()
+    _check(lib().dbnet_create(ctypes.byref(g), ctypes.cast(P, _vp), ctypes.byref(o),
+                              _stream(stream), ctypes.byref(h)), "dbnet_create")
+    return h
+
+
+def dbnet_step(h, n_steps: int) -> None:
+    _check(lib().dbnet_step(h, int(n_steps)), "dbnet_step")
+
+
+def dbnet_sync(h) -> None:
+    _check(lib().dbnet_sync(h), "dbnet_sync")
+
+
+def dbnet_stats(h) -> dict:
+    s = dbnet_stats_t()
+    _check(lib().dbnet_stats(h, ctypes.byref(s)), "dbnet_stats")
+    return {k: getattr(s, k) for k, _ in dbnet_stats_t._fields_}
+
+
+def dbnet_read_spikes(h, t0: int = 0, t1: int = 2**62, cap: int | None = None):
+    if cap is None:
+        cap = max(dbnet_stats(h)["raster_len"], 0)
+    st = np.zeros(max(cap, 1), dtype=np.int32)
+    ids = np.zeros(max(cap, 1), dtype=np.int32)
+    n = _i64(0)
+    _check(lib().dbnet_read_spikes(h, int(t0), int(t1), st.ctypes.data, ids.ctypes.data, int(cap),
+                                   ctypes.byref(n)), "dbnet_read_spikes")
+    return st[:n.value].copy(), ids[:n.value].copy()
+
+
+def dbnet_read_bold(h, n_regions: int, cap: int = 4096) -> np.ndarray:
+    y = np.zeros((max(cap, 1), n_regions))
+    n = _i64(0)
+    _check(lib().dbnet_read_bold(h, y.ctypes.data, int(cap), ctypes.byref(n)), "dbnet_read_bold")
+    return y[:n.value].copy()
+
+
+def dbnet_read_bw(h, n_regions: int) -> np.ndarray:
+    x = np.zeros((n_regions, 4))
+    _check(lib().dbnet_read_bw(h, x.ctypes.data), "dbnet_read_bw")
+    return x
+
+
+def dbnet_read_state(h, n_neurons: int):
+    V = np.zeros(n_neurons, dtype=np.float32)
+    J = np.zeros((4, n_neurons), dtype=np.float32)
+    ref = np.zeros(n_neurons, dtype=np.int32)
+    _check(lib().dbnet_read_state(h, V.ctypes.data, J.ctypes.data, ref.ctypes.data),
+           "dbnet_read_state")
+    return V, J, ref
+
+
+def dbnet_set_state(h, V=None, J=None, ref=None) -> None:
+    Va = None if V is None else np.ascontiguousarray(V, dtype=np.float32)
+    Ja = None if J is None else np.ascontiguousarray(J, dtype=np.float32)
+    ra = None if ref is None else np.ascontiguousarray(ref, dtype=np.int32)
+    _check(lib().dbnet_set_state(h, _addr(Va), _addr(Ja), _addr(ra)), "dbnet_set_state")
+
+
+def dbnet_destroy(h) -> None:
+    if h:
+        lib().dbnet_destroy(h)
+
+
+class Network:
+    """Owner of one dbnet handle."""
+
+    def __init__(self, graph, params, options=None, stream=None):
+        self.N = int(graph.n_neurons)
+        self.R = int(graph.n_regions)
+        self.h = dbnet_create(graph, params, options, stream)
+
+    def step(self, n: int) -> None:
+        dbnet_step(self.h, n)
+
+    def sync(self) -> None:
+        dbnet_sync(self.h)
+
+    def stats(self) -> dict:
+        return dbnet_stats(self.h)
+
+    def spikes(self, t0: int = 0, t1: int = 2**62):
+        return dbnet_read_spikes(self.h, t0, t1)
+
+    def bold(self, cap: int = 4096) -> np.ndarray:
+        return dbnet_read_bold(self.h, self.R, cap)
+
+    def bw(self) -> np.ndarray:
+        return dbnet_read_bw(self.h, self.R)
+
+    def state(self):
+        return dbnet_read_state(self.h, self.N)
+
+    def set_state(self, V=None, J=None, ref=None) -> None:
+        dbnet_set_state(self.h, V, J, ref)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            dbnet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

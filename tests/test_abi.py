@@ -1,0 +1,94 @@
+"""The C-ABI library loads and exports every entry point include/dbnet.h
+declares, and rejects malformed inputs on the host before any device work
+(these tests make no compute calls and run without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2211_15963_gb300 import dbnet
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b((?:dbnet|ens)_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return dbnet.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 18
+    raw = ctypes.CDLL(dbnet.library_path())
+    for n in names:
+        assert hasattr(raw, n), n
+    assert set(names) <= set(dbnet._SIGS), "binding misses a declared function"
+
+
+def test_strerror_and_defaults(lib):
+    for code in range(0, -9, -1):
+        assert lib.dbnet_strerror(code)
+    o = dbnet.dbnet_options_default()
+    assert o.dt_ms == 0.1 and o.bin_ms == 1.0 and o.tr_ms == 800.0 and o.precision == 32
+    assert abs(o.bw_rho - 0.34) < 1e-15 and o.bold_capacity == 4096
+
+
+def _tiny_graph():
+    W = np.zeros((6, 6))
+    W[1, 0] = 0.5
+    W[2, 1] = 0.25
+    return synth.graph_from_dense(W, np.full((6, 6), 2), [4, 2])
+
+
+def _expect(code, graph, params=None, **opts):
+    params = params or synth.default_region_params()
+    with pytest.raises(dbnet.DbnetError) as ei:
+        dbnet.dbnet_create(graph, params, opts)
+    assert ei.value.code == code, str(ei.value)
+
+
+def test_host_validation_rejects_malformed_inputs(lib):
+    g = _tiny_graph()
+    bad = _tiny_graph()
+    bad.region_offsets = np.array([0, 4, 7], dtype=np.int32)
+    _expect(dbnet.DBNET_EINVAL, bad)
+    bad = _tiny_graph()
+    bad.region_offsets = np.array([0, 6, 6], dtype=np.int32)
+    _expect(dbnet.DBNET_EINVAL, bad)
+    bad = _tiny_graph()
+    bad.n_exc = np.array([5, 1], dtype=np.int32)
+    _expect(dbnet.DBNET_EINVAL, bad)
+    bad = _tiny_graph()
+    bad.row_ptr = bad.row_ptr.copy()
+    bad.row_ptr[3] = bad.row_ptr[4] + 1
+    _expect(dbnet.DBNET_EINVAL, bad)
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(C=0.0))
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(tau_u=(2.0, -1.0, 10.0, 100.0)))
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(Tref=30.0))  # 300 steps > 255
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(w_ext=-1.0))
+    _expect(dbnet.DBNET_EINVAL, g, bin_ms=0.25)
+    _expect(dbnet.DBNET_EINVAL, g, tr_ms=800.5)
+    _expect(dbnet.DBNET_EUNSUPPORTED, g, precision=64)
+    _expect(dbnet.DBNET_EINVAL, g, fixed_shift=31)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(dbnet, "_lib", None)
+    monkeypatch.setattr(dbnet, "_SO", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        dbnet.lib()

@@ -1,0 +1,255 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+In the op-order-matched FP32 mode the device and the oracle perform the same
+IEEE operations in the same order and accumulate spikes in exact integers,
+so rasters, membrane potentials, traces and refractory counters must be
+bit-identical (the paper's own check is identical spike times and V within
+1e-4 of a CPU run of the same graph; Discussion of Extended Data Fig. 1).
+The BOLD readout is FP64 on both sides and agrees to 1e-10 relative.
+Long runs are compared with the FP64 oracle statistically (rates, ISI CV,
+BOLD correlation).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import metrics
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _net(g, p, **opts):
+    from paper_2211_15963_gb300 import dbnet
+    opts.setdefault("raster_capacity", 1 << 22)
+    return dbnet.Network(g, p, opts)
+
+
+def _assert_same_state(net, ref, where=""):
+    V, J, r = net.state()
+    Vo, Jo, ro = ref.state()
+    bad = np.flatnonzero(V.astype(np.float64) != Vo)
+    assert len(bad) == 0, "%s: V differs at %d neurons, first %s (%r vs %r)" % (
+        where, len(bad), bad[:5], V[bad[:3]], Vo[bad[:3]])
+    assert np.array_equal(J.astype(np.float64), Jo), where + ": traces differ"
+    assert np.array_equal(r, ro), where + ": refractory counters differ"
+
+
+def _delivered_by(g, st, ids, n_end):
+    """Edges of recorded spikes whose delay has come due before step n_end."""
+    rp = np.asarray(g.row_ptr)
+    d = np.asarray(g.delay).astype(np.int64)
+    tot = 0
+    for t, j in zip(st, ids):
+        seg = d[rp[j]:rp[j + 1]]
+        tot += int((t + seg <= n_end - 1).sum())
+    return tot
+
+
+def test_one_step_from_random_states(small_graph):
+    """Supp. Eqs. 3 and 5 from arbitrary states, step by step."""
+    g = small_graph
+    N = g.n_neurons
+    rng = np.random.default_rng(0)
+    V = rng.uniform(-75, -45, N).astype(np.float32)
+    J = rng.uniform(0, 3, (4, N)).astype(np.float32)
+    ref = rng.integers(0, 25, N).astype(np.int32) * (rng.random(N) < 0.2)
+    p = synth.default_region_params()
+    net = _net(g, p, seed=11)
+    o = oracle.Sim(g, p, seed=11, precision=32)
+    net.set_state(V, J, ref)
+    o.set_state(V.astype(np.float64), J.astype(np.float64), ref)
+    for k in range(25):
+        net.step(1)
+        o.step(1)
+        _assert_same_state(net, o, "step %d" % k)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 100 and np.array_equal(st, rs) and np.array_equal(ids, rids)
+
+
+def test_initial_state_matches_oracle(small_graph):
+    p = synth.default_region_params()
+    net = _net(small_graph, p, seed=5, net_id=9)
+    o = oracle.Sim(small_graph, p, seed=5, net_id=9, precision=32)
+    _assert_same_state(net, o, "initial")
+
+
+def test_small_network_raster_bit_exact_100ms(small_graph):
+    """10,000 neurons, in-degree 100, delays 1-20 steps: 100 ms (1000 steps)."""
+    g = small_graph
+    p = synth.default_region_params()
+    net = _net(g, p, seed=15964)
+    o = oracle.Sim(g, p, seed=15964, precision=32)
+    net.step(1000)
+    o.step(1000)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 1000
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "100 ms")
+    s = net.stats()
+    assert s["spikes"] == len(ids) == o.info()["spikes"]
+    assert s["events"] == _delivered_by(g, st, ids, 1000)
+    assert s["fixed_shift"] == o.info()["S"] == 16 and s["packed_edges"] == 1
+
+
+def test_small_network_one_second_and_bold(small_graph):
+    """The whole configured run (1 s): raster, state and FP64 BOLD."""
+    g = small_graph
+    p = synth.default_region_params()
+    net = _net(g, p, seed=15964, tr_ms=10.0)
+    o = oracle.Sim(g, p, seed=15964, tr_ms=10.0, precision=32)
+    for chunk in (64, 1, 999, 3000, 5936):   # graph replays and single launches
+        net.step(chunk)
+    o.step(10000)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "1 s")
+    y, yo = net.bold(), o.bold()
+    assert y.shape == yo.shape == (100, 1)
+    assert np.allclose(y, yo, rtol=1e-10, atol=1e-15)
+    assert np.allclose(net.bw(), o.bw_state(), rtol=1e-12, atol=1e-15)
+
+
+def test_multi_region_ragged_network():
+    """Several regions of uneven sizes (N not a multiple of the 1024-neuron
+    tile), cross-region delays up to 120 steps."""
+    g = synth.make_graph([1500, 700, 333, 2049], 80, 21, k_within=64, d_within=(1, 30),
+                         d_cross=(30, 120))
+    params = [synth.default_region_params(I_ext=0.8 + 0.05 * r) for r in range(g.n_regions)]
+    net = _net(g, params, seed=4, tr_ms=5.0)
+    o = oracle.Sim(g, params, seed=4, tr_ms=5.0, precision=32)
+    net.step(700)
+    o.step(700)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 500
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "multi-region")
+    assert np.allclose(net.bold(), o.bold(), rtol=1e-10, atol=1e-15)
+    assert net.stats()["events"] == _delivered_by(g, st, ids, 700)
+
+
+@pytest.mark.parametrize("sizes", [[1], [1025], [3, 1, 2]])
+def test_degenerate_sizes(sizes):
+    N = sum(sizes)
+    rng = np.random.default_rng(N)
+    W = np.where(rng.random((N, N)) < 0.5, 0.5, 0.0) if N > 1 else np.zeros((1, 1))
+    np.fill_diagonal(W, 0.0)
+    Dl = rng.integers(1, 6, (N, N))
+    g = synth.graph_from_dense(W, Dl, sizes) if N <= 64 else \
+        synth.make_graph(sizes, 10, 3, d_within=(1, 5))
+    p = synth.default_region_params(Tref=0.0)
+    net = _net(g, p, seed=2)
+    o = oracle.Sim(g, p, seed=2, precision=32)
+    net.step(200)
+    o.step(200)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "sizes %s" % sizes)
+
+
+def test_empty_graph_and_longest_delay():
+    """No edges at all; and a single edge of delay 255 (the longest)."""
+    W = np.zeros((8, 8))
+    g0 = synth.graph_from_dense(W, np.ones((8, 8), dtype=np.int64), [8])
+    p = synth.default_region_params()
+    net = _net(g0, p)
+    o = oracle.Sim(g0, p, precision=32)
+    net.step(300)
+    o.step(300)
+    _assert_same_state(net, o, "no edges")
+    W[3, 0] = 1.5
+    Dl = np.full((8, 8), 255)
+    g1 = synth.graph_from_dense(W, Dl, [8])
+    p1 = synth.default_region_params(I_ext=0.0, drive_rate_hz=0.0)
+    net = _net(g1, p1)
+    o = oracle.Sim(g1, p1, precision=32)
+    V0 = np.full(8, -70.0, dtype=np.float32)
+    V0[0] = -49.0
+    net.set_state(V0, np.zeros((4, 8), np.float32), np.zeros(8, np.int32))
+    o.set_state(V0.astype(np.float64), np.zeros((4, 8)), np.zeros(8, np.int32))
+    for _ in range(4):
+        net.step(100)
+        o.step(100)
+        _assert_same_state(net, o, "delay 255")
+    J = net.state()[1]
+    assert J[0, 3] > 0 and net.stats()["events"] == 1
+
+
+def test_device_validation_rejects_bad_edges():
+    from paper_2211_15963_gb300 import dbnet
+    W = np.zeros((6, 6))
+    W[1, 0] = 0.5
+    W[2, 0] = 0.25
+    base = synth.graph_from_dense(W, np.full((6, 6), 2), [6])
+    p = synth.default_region_params()
+
+    def expect(mut, code=dbnet.DBNET_EINVAL):
+        g = synth.graph_from_dense(W, np.full((6, 6), 2), [6])
+        mut(g)
+        with pytest.raises(dbnet.DbnetError) as ei:
+            dbnet.dbnet_create(g, p)
+        assert ei.value.code == code, str(ei.value)
+
+    expect(lambda g: g.col.__setitem__(0, 6))
+    expect(lambda g: g.col.__setitem__(0, -1))
+    expect(lambda g: g.delay.__setitem__(0, 0))
+    expect(lambda g: (g.delay.__setitem__(0, 5), g.delay.__setitem__(1, 2)))
+    expect(lambda g: g.w_bf16.__setitem__(1, 0xBF80))  # -1.0
+    expect(lambda g: g.w_bf16.__setitem__(1, 0x7FC0))  # NaN
+    assert base.n_edges == 2
+
+
+def test_float_weights_match_bf16_and_flag_rounding(small_graph):
+    from paper_2211_15963_gb300 import dbnet
+    g = small_graph
+    p = synth.default_region_params()
+
+    class F:  # same graph with float32 weights
+        n_neurons, n_regions = g.n_neurons, g.n_regions
+        region_offsets, n_exc, row_ptr, col, delay = g.region_offsets, g.n_exc, g.row_ptr, g.col, g.delay
+        weight = g.weights_f64().astype(np.float32)
+
+    a = _net(g, p, seed=8)
+    b = _net(F, p, seed=8)
+    a.step(300)
+    b.step(300)
+    assert np.array_equal(a.state()[0], b.state()[0])
+    assert b.stats()["weights_rounded"] == 0
+    F.weight = F.weight * np.float32(1.001)
+    c = dbnet.Network(F, p, dict(seed=8))
+    assert c.stats()["weights_rounded"] == 1
+
+
+def test_long_run_statistics_against_fp64_oracle(small_graph):
+    """North-star accuracy over long runs against the FP64 oracle: rate
+    within 2 %, ISI CV within 0.02, BOLD correlation >= 0.99."""
+    g = small_graph
+    p = synth.default_region_params()
+    T = 30000
+    net = _net(g, p, seed=15964, tr_ms=10.0, raster_capacity=1 << 23)
+    net.step(T)
+    o = oracle.Sim(g, p, seed=15964, tr_ms=10.0, precision=64)
+    o.step(T)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    r_gpu = len(ids) / g.n_neurons / (T * 1e-4)
+    r_64 = len(rids) / g.n_neurons / (T * 1e-4)
+    assert abs(r_gpu - r_64) / r_64 < 0.02, (r_gpu, r_64)
+    assert abs(metrics.isi_cv(st, ids) - metrics.isi_cv(rs, rids)) < 0.02
+    y, yo = net.bold()[:, 0], o.bold()[:, 0]
+    assert metrics.pcc(y, yo) >= 0.99
