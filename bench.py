@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the Digital Brain hot path on one GB300 (or N replicas).
+
+Workload: the mid-size network -- 2,000,000 conductance LIF neurons in 100
+regions of 20,000 (80 % E / 20 % I), in-degree 1,000 (800 within the region,
+200 from excitatory neurons of other regions drawn from a seeded 100x100
+region matrix of density 0.3), BF16 lognormal weights, delays 0.1-5 ms within
+and 5-20 ms across regions, dt = 0.1 ms, drive tuned to ~7 / 15 / 30 Hz
+(--rate).  Synthetic, seeded.  One benchmark step = one biological second
+(10,000 Euler steps: update, compaction, delivery, region counts, BOLD).
+
+Metric: synaptic events per second (events applied to the accumulators,
+counted on the device).  Also reported: real-time factor (wall s per
+biological s), neuron updates/s, per-kernel roofline against the measured
+HBM copy bandwidth, the end-to-end figure through the C ABI from pinned host
+buffers, and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--rate 7|15|30]
+  python bench.py --impl reference ...   # the CPU oracle as the reference arm
+For N > 1, launch with torch.distributed.run; each rank runs an independent
+replica (the path does not shard: replicas only) and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+STEPS_PER_BIO_S = 10_000  # dt = 0.1 ms
+# Constant current that puts the in-degree-1000 network at the target rate,
+# found with paper_2211_15963_gb300.tune.tune_drive on a 1/20 sub-network
+# (5 regions of 20,000): 6.9, 14.7 and 29.4 Hz there.
+RATE_DRIVE = {7: 3.1757, 15: 7.2221, 30: 16.4246}
+UPDATE_BYTES_PER_NEURON = 58   # V r/w 8, J r/w 32, ref r/w 2, accumulator read + clear 16
+DELIVER_BYTES_PER_EVENT = 14   # target|delay 4 + BF16 weight 2 + int32 read-modify-write 8
+METRIC = "synaptic events/s"
+UNIT = "events/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--rate", type=int, default=15, choices=sorted(RATE_DRIVE))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--profile-steps", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--regions", type=int, default=100, help="regions of 20,000 neurons")
+    ap.add_argument("--k-in", type=int, default=1000, help="in-degree (80 %% within region)")
+    return ap.parse_args()
+
+
+def workload_config(args, rank_count):
+    return {"workload": "mid-size network: %d neurons, %d regions x 20,000, in-degree %d, "
+                        "dt 0.1 ms, ~%d Hz" % (args.regions * 20000, args.regions, args.k_in,
+                                                args.rate),
+            "neurons": args.regions * 20000, "regions": args.regions, "in_degree": args.k_in,
+            "dt_ms": 0.1, "target_rate_hz": args.rate, "step": "1 biological second",
+            "replicas": rank_count,
+            "l2": "flushed (256 MiB write) between timed steps; edge arrays exceed L2"}
+
+
+def params_for(rate, k_in=1000):
+    import synth
+    p = synth.scale_for_degree(synth.default_region_params(), k_in)
+    p["I_ext"] = RATE_DRIVE[rate]
+    return p
+
+
+# ----------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers ----
+def kernels_sha():
+    p = os.path.join(ROOT, "paper_2211_15963_gb300", "csrc", "kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, when
+    it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic_mid_network.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernels_sha") != kernels_sha():
+        return None
+    return d.get("bytes_per_launch", {}).get(kernel)
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def pinned_alloc(torch):
+    import numpy as np
+    keep = []
+
+    def alloc(n, dt):
+        t = torch.empty(n, dtype={np.int32: torch.int32, np.uint16: torch.int16,
+                                  np.uint8: torch.uint8}[dt], pin_memory=True)
+        keep.append(t)
+        return t
+    return alloc, keep
+
+
+def oracle_sample(params, seconds=12.0):
+    """The CPU oracle (matched FP32, single thread) on a 1/20-scale sample of
+    the workload: 5 regions of 20,000 neurons, in-degree 1,000, same drive.
+    200 ms are simulated untimed to pass the onset transient, then whole
+    1 ms chunks are timed until `seconds` of CPU time have elapsed."""
+    import oracle
+    import synth
+    g = synth.mid_network(n_regions=5, seed=synth.seed_for(1) + 100)
+    s = oracle.Sim(g, params, seed=synth.seed_for(1) + 1, precision=32)
+    s.step(2000)
+    i0 = s.info()
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        s.step(10)
+        steps += 10
+    wall = time.perf_counter() - t0
+    i1 = s.info()
+    ev = i1["events"] - i0["events"]
+    return {"value": ev / wall, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "neuron_updates_per_s": g.n_neurons * steps / wall,
+            "sample": "%d steps (%.0f ms biological) of a 100,000-neuron, in-degree-1,000 "
+                      "1/20-scale network after a 200 ms untimed onset; single-threaded "
+                      "matched-FP32 oracle" % (steps, steps * 0.1)}
+
+
+# -------------------------------------------------------------- our arm ----
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    import __graft_entry__
+    from paper_2211_15963_gb300 import dbnet
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)  # the library and every event use this stream
+
+    alloc, keep = pinned_alloc(torch)
+    seed = synth.seed_for(1) + 1000 * rank
+    t_gen = time.perf_counter()
+    g = synth.make_graph([20000] * args.regions, args.k_in, seed, k_within=int(round(0.8 * args.k_in)),
+                         d_within=(1, 50), d_cross=(50, 200), alloc=alloc)
+    t_gen = time.perf_counter() - t_gen
+    params = params_for(args.rate, args.k_in)
+    opts = dict(seed=seed + 1, net_id=rank)
+
+    net = dbnet.Network(g, params, opts, stream)
+    for _ in range(args.warmup):
+        net.step(STEPS_PER_BIO_S)
+    net.sync()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    s0 = net.stats()
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        starts[k].record(stream)
+        net.step(STEPS_PER_BIO_S)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    s1 = net.stats()
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    events = s1["events"] - s0["events"]
+    spikes = s1["spikes"] - s0["spikes"]
+    tot = torch.tensor([events, spikes, g.n_neurons], dtype=torch.float64, device=dev)
+    mx = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    events_all, spikes_all, neurons_all = (float(x) for x in tot.tolist())
+    ms_all = float(mx.item())
+    ms_per_step = ms_all / args.steps
+    value = events_all / (ms_all * 1e-3)
+
+    # per-kernel device time (each kernel between CUDA events on the stream)
+    p0 = net.stats()
+    t_del, t_upd = net.step_timed(args.profile_steps)
+    p1 = net.stats()
+    n_prof = args.profile_steps
+    ev_per_launch = (p1["events"] - p0["events"]) / n_prof
+    hbm, peak_kind = peaks()
+    upd_bytes = g.n_neurons * UPDATE_BYTES_PER_NEURON
+    del_bytes = ev_per_launch * DELIVER_BYTES_PER_EVENT
+    kern = {
+        "k_update": {"avg_us": 1e3 * t_upd / n_prof, "algorithmic_bytes": upd_bytes,
+                     "achieved_gbs": upd_bytes / (t_upd / n_prof * 1e-3) / 1e9,
+                     "traffic": measured_traffic("k_update")},
+        "k_deliver": {"avg_us": 1e3 * t_del / n_prof, "algorithmic_bytes": del_bytes,
+                      "events_per_launch": ev_per_launch,
+                      "achieved_gbs": del_bytes / (t_del / n_prof * 1e-3) / 1e9,
+                      "traffic": measured_traffic("k_deliver")},
+    }
+    dom = "k_update" if t_upd >= t_del else "k_deliver"
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / hbm, "traffic": kern[dom]["traffic"],
+            "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "kernels": kern}
+    net.close()
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h2d = (g.row_ptr.nbytes + 4 * g.n_edges + 2 * g.n_edges + g.n_edges +
+               g.region_offsets.nbytes + g.n_exc.nbytes + 200 * g.n_regions)
+        d2h = 8 * g.n_regions + 96
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ev_e2e = 0
+        for _ in range(args.e2e_steps):
+            h = dbnet.dbnet_create(g, params, opts, stream)
+            dbnet.dbnet_step(h, STEPS_PER_BIO_S)
+            st = dbnet.dbnet_stats(h)
+            y = dbnet.dbnet_read_bold(h, g.n_regions, 4)
+            ev_e2e += st["events"]
+            dbnet.dbnet_destroy(h)
+        torch.cuda.synchronize()
+        t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        ev_t = torch.tensor([float(ev_e2e)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+            dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+        e2e = {"value": float(ev_t.item()) / float(t_e2e.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "what": "dbnet_create from pinned host graph + 1 biological second + stats and "
+                       "BOLD read + destroy, per step (includes the onset transient)",
+               "steps": args.e2e_steps, "bold_samples": int(len(y))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(params)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators, f64 BOLD",
+            "data": "synthetic (seeded generator)", "config": workload_config(args, world),
+            "rtf": ms_per_step / 1e3,
+            "neuron_updates_per_s": neurons_all * STEPS_PER_BIO_S * args.steps / (ms_all * 1e-3),
+            "mean_rate_hz": spikes_all / neurons_all / args.steps,
+            "wall_s_timed": wall, "generate_s": t_gen,
+            "clocks": clk, "e2e": e2e, "gpu_launches": 2 * STEPS_PER_BIO_S * args.steps,
+            "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------- reference arm ----
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores: each step is a 10 ms
+    (100 Euler steps) sample of the 1/20-scale network after an untimed
+    200 ms onset.  Under torchrun only rank 0 works."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    synth.build()
+    params = params_for(args.rate)
+    g = synth.mid_network(n_regions=5, seed=synth.seed_for(1) + 100)
+    s = oracle.Sim(g, params, seed=synth.seed_for(1) + 1, precision=32)
+    s.step(2000)
+    for _ in range(args.warmup):
+        s.step(100)
+    i0 = s.info()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(100)
+    wall = time.perf_counter() - t0
+    i1 = s.info()
+    ev = i1["events"] - i0["events"]
+    value = ev / wall
+    sample = ("%d x 100 Euler steps (10 ms biological each) of a 100,000-neuron, "
+              "in-degree-1,000 1/20-scale network after a 200 ms untimed onset" % args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (op-order-matched oracle)", "data": "synthetic (seeded generator)",
+        "config": workload_config(args, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,13 @@ int dbnet_step(dbnet_t* h, int64_t n_steps);
 /* Wait for the handle's stream. */
 int dbnet_sync(dbnet_t* h);
 
+/* Measurement form of dbnet_step: the same n_steps, but every kernel is
+ * launched on its own (no graph replay) between CUDA events recorded on the
+ * handle's stream.  Waits for completion, then ms[0] = summed device time of
+ * the delivery kernel and ms[1] = of the neuron-update kernel over the
+ * n_steps launches of each.  Results are identical to dbnet_step. */
+int dbnet_step_timed(dbnet_t* h, int64_t n_steps, double* ms);
+
 /* Recorded spikes with t0 <= step < t1, sorted by (step, id), written to
  * step[] and id[] (capacity cap).  *n_out = number written; DBNET_ERANGE
  * when more than cap match (the first cap are written). */

@@ -416,6 +416,43 @@ void Engine::step(int64_t n) {
   CK(cudaGetLastError());
 }
 
+void Engine::step_timed(int64_t n, double* ms) {
+  check();
+  if (n < 0) raise(DBNET_EINVAL, "n_steps must be >= 0");
+  constexpr int kPool = 512;  // steps per batch of events
+  std::vector<cudaEvent_t> ev(3 * kPool, nullptr);
+  for (auto& x : ev) CK(cudaEventCreate(&x));
+  double t_del = 0.0, t_upd = 0.0;
+  try {
+    while (n > 0) {
+      const int b = (int)std::min<int64_t>(n, kPool);
+      for (int i = 0; i < b; ++i) {
+        CK(cudaEventRecord(ev[3 * i], stream));
+        launch_deliver(dev, del_grid, stream);
+        CK(cudaEventRecord(ev[3 * i + 1], stream));
+        launch_update(dev, stream);
+        CK(cudaEventRecord(ev[3 * i + 2], stream));
+      }
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(stream));
+      for (int i = 0; i < b; ++i) {
+        float a = 0.f, c = 0.f;
+        CK(cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]));
+        CK(cudaEventElapsedTime(&c, ev[3 * i + 1], ev[3 * i + 2]));
+        t_del += a;
+        t_upd += c;
+      }
+      n -= b;
+    }
+  } catch (...) {
+    for (auto& x : ev) cudaEventDestroy(x);
+    throw;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  ms[0] = t_del;
+  ms[1] = t_upd;
+}
+
 void Engine::sync() {
   check();
   CK(cudaStreamSynchronize(stream));
@@ -534,6 +571,11 @@ int dbnet_create(const dbnet_graph_t* graph, const dbnet_region_params_t* params
 int dbnet_step(dbnet_t* h, int64_t n_steps) {
   if (!h || !h->own) return DBNET_EINVAL;
   return guarded(h->eng, [&] { h->eng->step(n_steps); });
+}
+
+int dbnet_step_timed(dbnet_t* h, int64_t n_steps, double* ms) {
+  if (!h || !h->own || !ms) return DBNET_EINVAL;
+  return guarded(h->eng, [&] { h->eng->step_timed(n_steps, ms); });
 }
 
 int dbnet_sync(dbnet_t* h) {

@@ -131,6 +131,7 @@ struct Engine {
   void check() const;
   void capture();
   void step(int64_t n);
+  void step_timed(int64_t n, double* ms);
   void sync();
   InstDyn read_dyn(int k);
 };

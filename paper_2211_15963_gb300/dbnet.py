@@ -76,6 +76,7 @@ _SIGS = {
                                     ctypes.POINTER(dbnet_options_t), _vp, ctypes.POINTER(_vp)]),
     "dbnet_step": (ctypes.c_int, [_vp, _i64]),
     "dbnet_sync": (ctypes.c_int, [_vp]),
+    "dbnet_step_timed": (ctypes.c_int, [_vp, _i64, _vp]),
     "dbnet_read_spikes": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "dbnet_read_bold": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
     "dbnet_read_bw": (ctypes.c_int, [_vp, _vp]),
@@ -227,6 +228,13 @@ def dbnet_step(h, n_steps: int) -> None:
     _check(lib().dbnet_step(h, int(n_steps)), "dbnet_step")
 
 
+def dbnet_step_timed(h, n_steps: int):
+    """Returns (delivery ms, update ms) summed over the n_steps launches."""
+    ms = np.zeros(2)
+    _check(lib().dbnet_step_timed(h, int(n_steps), ms.ctypes.data), "dbnet_step_timed")
+    return float(ms[0]), float(ms[1])
+
+
 def dbnet_sync(h) -> None:
     _check(lib().dbnet_sync(h), "dbnet_sync")
 
@@ -295,6 +303,9 @@ class Network:
 
     def sync(self) -> None:
         dbnet_sync(self.h)
+
+    def step_timed(self, n: int):
+        return dbnet_step_timed(self.h, n)
 
     def stats(self) -> dict:
         return dbnet_stats(self.h)
