@@ -243,6 +243,58 @@ int ens_member(dbens_t* h, int32_t member, dbnet_t** out);
 
 void ens_destroy(dbens_t* h);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free run.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory once they are running --
+ * for instance code inside a framework whose arena owns all device memory,
+ * or a closed loop that must not pay cudaMalloc's implicit device-wide
+ * synchronisation.  It performs no cudaMalloc, cudaFree or other allocating
+ * call.  Its scratch (live delivery lists, accumulators, counters, region
+ * constants) is one static device array of DBNET_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading this library holds until the process exits.
+ *
+ * Graph: row_ptr, col, weight_bf16 and delay are DEVICE arrays in the same
+ * layout as dbnet_graph_t (delays non-decreasing within a row); they are
+ * validated on the device and never modified.  region_offsets and n_exc are
+ * HOST arrays.
+ * Run: the network starts from the same initial state as dbnet_create (V
+ * uniform in [V_reset, V_th) from Philox stream 1, traces zero, no spike in
+ * flight) and advances n_steps exactly as dbnet_step does.
+ * Outputs (DEVICE arrays owned by the caller): V[n_pad], J[4][n_pad]
+ * (channel-major, row stride n_pad), ref[n_pad] (u8), with n_pad = N rounded
+ * up to a multiple of 1024; raster_step/raster_id[raster_cap] receive the
+ * spikes (unordered within a step; more than raster_cap are dropped and
+ * counted).  *n_spikes and *n_events (host) receive the totals.
+ * Limits: N <= DBNET_NOALLOC_MAX_NEURONS, R <= DBNET_NOALLOC_MAX_REGIONS and
+ * N * ceil(255 / (min refractory steps + 1)) <= DBNET_NOALLOC_MAX_LIVE
+ * (the live-list bound); larger inputs return DBNET_ERANGE.
+ * Set-up: the first call on each device looks up the scratch address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  The call waits for its work to finish.
+ * Every call reuses the same scratch and clears it first, so calls that
+ * overlap on the GPU (from several threads or streams) race. */
+#define DBNET_NOALLOC_MAX_NEURONS 65536
+#define DBNET_NOALLOC_MAX_REGIONS 64
+#define DBNET_NOALLOC_MAX_LIVE (1 << 19)
+#define DBNET_NOALLOC_SCRATCH_BYTES (18u << 20)
+
+typedef struct {
+  int32_t n_neurons;
+  int32_t n_regions;
+  const int32_t* region_offsets; /* host [R+1] */
+  const int32_t* n_exc;          /* host [R] */
+  const int64_t* row_ptr;        /* device [N+1] */
+  const int32_t* col;            /* device [E] */
+  const uint16_t* weight_bf16;   /* device [E] */
+  const uint8_t* delay;          /* device [E] */
+} dbnet_device_graph_t;
+
+int dbnet_run_noalloc(const dbnet_device_graph_t* graph, const dbnet_region_params_t* params,
+                      const dbnet_options_t* options, int64_t n_steps, float* V, float* J,
+                      uint8_t* ref, int32_t* raster_step, int32_t* raster_id,
+                      int64_t raster_cap, int64_t* n_spikes, int64_t* n_events,
+                      void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

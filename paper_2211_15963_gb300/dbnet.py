@@ -63,6 +63,12 @@ class dbnet_stats_t(ctypes.Structure):
                 ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32)]
 
 
+class dbnet_device_graph_t(ctypes.Structure):
+    _fields_ = [("n_neurons", _i32), ("n_regions", _i32), ("region_offsets", _vp),
+                ("n_exc", _vp), ("row_ptr", _vp), ("col", _vp), ("weight_bf16", _vp),
+                ("delay", _vp)]
+
+
 class dbens_enkf_t(ctypes.Structure):
     _fields_ = [("obs_var", _d), ("gamma", _d), ("rw_sigma", _d), ("theta_lo", _d),
                 ("theta_hi", _d), ("floor", _d), ("mode", _i32)]
@@ -92,6 +98,10 @@ _SIGS = {
     "ens_read": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "ens_member": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp)]),
     "ens_destroy": (None, [_vp]),
+    "dbnet_run_noalloc": (ctypes.c_int, [ctypes.POINTER(dbnet_device_graph_t), _vp,
+                                         ctypes.POINTER(dbnet_options_t), _i64, _vp, _vp, _vp,
+                                         _vp, _vp, _i64, ctypes.POINTER(_i64),
+                                         ctypes.POINTER(_i64), _vp]),
 }
 
 
@@ -341,3 +351,32 @@ class Network:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------- allocation-free ----
+def dbnet_run_noalloc(n_neurons, region_offsets, n_exc, row_ptr, col, weight_bf16, delay, params,
+                      options, n_steps, V, J, ref, raster_step=None, raster_id=None, stream=None):
+    """Run through the allocation-free entry point.  row_ptr, col,
+    weight_bf16, delay, V [n_pad], J [4, n_pad], ref [n_pad] (uint8) and the
+    optional raster buffers are CUDA tensors the caller allocated;
+    region_offsets and n_exc are host arrays.  Returns (n_spikes, n_events)."""
+    def dptr(t):
+        if t is None:
+            return 0
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA tensor")
+        return int(t.data_ptr())
+    ro = np.ascontiguousarray(region_offsets, dtype=np.int32)
+    ne = np.ascontiguousarray(n_exc, dtype=np.int32)
+    R = len(ne)
+    g = dbnet_device_graph_t(int(n_neurons), R, ro.ctypes.data, ne.ctypes.data, dptr(row_ptr),
+                             dptr(col), dptr(weight_bf16), dptr(delay))
+    P = params_array(params, R)
+    o = options_from(options)
+    cap = 0 if raster_step is None else int(raster_step.numel())
+    ns, ne_ = _i64(0), _i64(0)
+    _check(lib().dbnet_run_noalloc(ctypes.byref(g), ctypes.cast(P, _vp), ctypes.byref(o),
+                                   int(n_steps), dptr(V), dptr(J), dptr(ref), dptr(raster_step),
+                                   dptr(raster_id), cap, ctypes.byref(ns), ctypes.byref(ne_),
+                                   _stream(stream)), "dbnet_run_noalloc")
+    return ns.value, ne_.value
