@@ -474,11 +474,6 @@ InstDyn Engine::read_dyn(int k) {
 // ------------------------------------------------------------------ ABI ----
 using namespace dbn;
 
-struct dbnet {
-  std::unique_ptr<Engine> own;  // null for a member view of an ensemble
-  Engine* eng = nullptr;
-  int inst = 0;
-};
 
 template <class F>
 static int guarded(Engine* eng, F&& f) {

@@ -143,3 +143,10 @@ RegionConst region_const(const dbnet_region_params_t& p, double dt, int S, int32
                          int32_t end, int32_t exc_end);
 
 }  // namespace dbn
+
+// A network handle: owns its engine, or views one instance of an ensemble.
+struct dbnet {
+  std::unique_ptr<dbn::Engine> own;  // null for a member view of an ensemble
+  dbn::Engine* eng = nullptr;
+  int inst = 0;
+};

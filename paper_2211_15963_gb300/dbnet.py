@@ -380,3 +380,103 @@ def dbnet_run_noalloc(n_neurons, region_offsets, n_exc, row_ptr, col, weight_bf1
                                    dptr(raster_id), cap, ctypes.byref(ns), ctypes.byref(ne_),
                                    _stream(stream)), "dbnet_run_noalloc")
     return ns.value, ne_.value
+
+
+# -------------------------------------------------------------- ensemble ----
+def enkf_options(obs_var=1e-6, gamma=0.5, rw_sigma=0.02, theta_lo=-0.6931471805599453,
+                 theta_hi=0.6931471805599453, floor=1e-2, mode=DBENS_DIFFUSION) -> dbens_enkf_t:
+    return dbens_enkf_t(obs_var, gamma, rw_sigma, theta_lo, theta_hi, floor, mode)
+
+
+def ens_create(graph, base_params, n_members: int, log_scale_init, options=None, enkf=None,
+               stream=None):
+    g, keep = graph_struct(graph)
+    P = params_array(base_params, int(graph.n_regions))
+    o = options_from(options)
+    th = np.ascontiguousarray(log_scale_init, dtype=np.float64)
+    assert th.shape == (n_members, int(graph.n_regions), 2)
+    k = enkf if isinstance(enkf, dbens_enkf_t) else enkf_options(**(enkf or {}))
+    h = _vp()
+    _check(lib().ens_create(ctypes.byref(g), ctypes.cast(P, _vp), int(n_members), th.ctypes.data,
+                            ctypes.byref(o), ctypes.byref(k), _stream(stream), ctypes.byref(h)),
+           "ens_create")
+    return h
+
+
+def ens_step(h, n_steps: int) -> None:
+    _check(lib().ens_step(h, int(n_steps)), "ens_step")
+
+
+def ens_assimilate(h, y_obs, n_members: int, eps_obs=None, xi_rw=None) -> np.ndarray:
+    y = np.ascontiguousarray(y_obs, dtype=np.float64)
+    R = len(y)
+    e = None if eps_obs is None else np.ascontiguousarray(eps_obs, dtype=np.float64)
+    x = None if xi_rw is None else np.ascontiguousarray(xi_rw, dtype=np.float64)
+    if e is not None:
+        assert e.shape == (n_members, R)
+    if x is not None:
+        assert x.shape == (n_members, R, 2)
+    out = np.zeros(R)
+    _check(lib().ens_assimilate(h, y.ctypes.data, _addr(e), _addr(x), out.ctypes.data),
+           "ens_assimilate")
+    return out
+
+
+def ens_read(h, n_members: int, n_regions: int):
+    th = np.zeros((n_members, n_regions, 2))
+    bw = np.zeros((n_members, n_regions, 4))
+    y = np.zeros((n_members, n_regions))
+    _check(lib().ens_read(h, th.ctypes.data, bw.ctypes.data, y.ctypes.data), "ens_read")
+    return th, bw, y
+
+
+def ens_member(h, member: int):
+    v = _vp()
+    _check(lib().ens_member(h, int(member), ctypes.byref(v)), "ens_member")
+    return v
+
+
+def ens_destroy(h) -> None:
+    if h:
+        lib().ens_destroy(h)
+
+
+class Ensemble:
+    """Owner of one dbens handle (M networks sharing a graph)."""
+
+    def __init__(self, graph, base_params, n_members, log_scale_init, options=None, enkf=None,
+                 stream=None):
+        self.M = int(n_members)
+        self.R = int(graph.n_regions)
+        self.N = int(graph.n_neurons)
+        self.h = ens_create(graph, base_params, n_members, log_scale_init, options, enkf, stream)
+
+    def step(self, n: int) -> None:
+        ens_step(self.h, n)
+
+    def assimilate(self, y_obs, eps_obs=None, xi_rw=None) -> np.ndarray:
+        return ens_assimilate(self.h, y_obs, self.M, eps_obs, xi_rw)
+
+    def read(self):
+        return ens_read(self.h, self.M, self.R)
+
+    def member_state(self, m: int):
+        return dbnet_read_state(ens_member(self.h, m), self.N)
+
+    def member_bold(self, m: int, cap: int = 4096):
+        return dbnet_read_bold(ens_member(self.h, m), self.R, cap)
+
+    def member_spikes(self, m: int):
+        v = ens_member(self.h, m)
+        return dbnet_read_spikes(v)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            ens_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

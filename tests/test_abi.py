@@ -92,3 +92,23 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dbnet, "_SO", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         dbnet.lib()
+
+
+def test_ensemble_host_validation(lib):
+    g = _tiny_graph()
+    p = synth.default_region_params()
+    th = np.zeros((3, 2, 2))
+
+    def expect(code, M=3, theta=th, **k):
+        with pytest.raises(dbnet.DbnetError) as ei:
+            dbnet.ens_create(g, p, M, theta if theta.shape[0] == M else np.zeros((M, 2, 2)), {},
+                             dbnet.enkf_options(**k))
+        assert ei.value.code == code, str(ei.value)
+
+    expect(dbnet.DBNET_EINVAL, M=1)
+    expect(dbnet.DBNET_EINVAL, obs_var=0.0)
+    expect(dbnet.DBNET_EINVAL, gamma=1.5)
+    expect(dbnet.DBNET_EINVAL, rw_sigma=-1.0)
+    expect(dbnet.DBNET_EINVAL, theta_lo=1.0, theta_hi=0.0)
+    expect(dbnet.DBNET_EINVAL, mode=7)
+    expect(dbnet.DBNET_EINVAL, theta=np.full((3, 2, 2), np.nan))
