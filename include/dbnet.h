@@ -14,8 +14,9 @@
  *     freed by the matching *_destroy.  Output arrays are caller-allocated
  *     host memory.
  *   - Streams: all device work is enqueued on the CUDA stream given at
- *     create (NULL = the legacy default stream); step calls return without
- *     waiting, read calls synchronise that stream first.
+ *     create (NULL = a non-blocking stream the handle creates and owns);
+ *     step calls return without waiting, read calls synchronise that stream
+ *     first.
  *   - Threads: a handle must not be used from two threads at once.
  *   - Units: mV, ms, nF, microsiemens, nA; BOLD model constants in seconds.
  *   - Neuron numbering: neurons are sorted by region; inside a region the
@@ -148,6 +149,7 @@ int dbnet_options_default(dbnet_options_t* o);
  * validate them on the device, pack the edges (target and delay in one
  * 32-bit word when N <= 2^24, BF16 weight), choose S and set the initial
  * state (V uniform in [V_reset, V_th) from Philox stream 1; traces zero).
+ * Also builds the per-row delay-segment table (N x longest delay counts).
  * params: [n_regions].  cuda_stream: a cudaStream_t or NULL.
  * Returns DBNET_EINVAL for a malformed graph or parameter set,
  * DBNET_EOVERFLOW when the chosen S could overflow, DBNET_ENOMEM, DBNET_ECUDA. */
@@ -249,9 +251,9 @@ void ens_destroy(dbens_t* h);
  * for instance code inside a framework whose arena owns all device memory,
  * or a closed loop that must not pay cudaMalloc's implicit device-wide
  * synchronisation.  It performs no cudaMalloc, cudaFree or other allocating
- * call.  Its scratch (live delivery lists, accumulators, counters, region
- * constants) is one static device array of DBNET_NOALLOC_SCRATCH_BYTES that
- * every GPU loading this library holds until the process exits.
+ * call.  Its scratch (spike ring, accumulators, counters, region constants)
+ * is one static device array of DBNET_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits.
  *
  * Graph: row_ptr, col, weight_bf16 and delay are DEVICE arrays in the same
  * layout as dbnet_graph_t (delays non-decreasing within a row); they are
@@ -266,8 +268,8 @@ void ens_destroy(dbens_t* h);
  * spikes (unordered within a step; more than raster_cap are dropped and
  * counted).  *n_spikes and *n_events (host) receive the totals.
  * Limits: N <= DBNET_NOALLOC_MAX_NEURONS, R <= DBNET_NOALLOC_MAX_REGIONS and
- * N * ceil(255 / (min refractory steps + 1)) <= DBNET_NOALLOC_MAX_LIVE
- * (the live-list bound); larger inputs return DBNET_ERANGE.
+ * n_pad * (longest delay + 1) <= DBNET_NOALLOC_MAX_LIVE (the spike ring);
+ * larger inputs return DBNET_ERANGE.
  * Set-up: the first call on each device looks up the scratch address with
  * cudaGetSymbolAddress while that device is current; make that first call
  * before any stream capture.  The call waits for its work to finish.
@@ -275,7 +277,7 @@ void ens_destroy(dbens_t* h);
  * overlap on the GPU (from several threads or streams) race. */
 #define DBNET_NOALLOC_MAX_NEURONS 65536
 #define DBNET_NOALLOC_MAX_REGIONS 64
-#define DBNET_NOALLOC_MAX_LIVE (1 << 19)
+#define DBNET_NOALLOC_MAX_LIVE (1 << 22)
 #define DBNET_NOALLOC_SCRATCH_BYTES (18u << 20)
 
 typedef struct {

@@ -3,7 +3,8 @@
 // Create: host-side checks that cost O(N + R), then the edge arrays are
 // copied to the device, validated and packed by one warp-per-row kernel
 // (target range, delay range and order, weights -> BF16, in-degrees, largest
-// weight and delay), the fixed-point scale is chosen from those, the region
+// weight and delay), the per-delay segment table of every row is built, the
+// fixed-point scale is chosen from those, the region
 // constants are derived in FP64 and rounded to FP32 once, and the initial
 // state is drawn on the device.
 //
@@ -106,6 +107,16 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   gd->w_max = (double)wmax;
   gd->max_delay = (int32_t)std::max(1u, h[1]);
   gd->kin_max = (int32_t)h[3];
+  // segment table: u16 counts when every row has fewer than 2^16 edges
+  int64_t max_out = 0;
+  for (int32_t j = 0; j < N; ++j) max_out = std::max(max_out, g->row_ptr[j + 1] - g->row_ptr[j]);
+  gd->seg_kind = max_out < 65536 ? kSeg16 : kSeg32;
+  const int64_t seg_bytes = (int64_t)N * gd->max_delay * (gd->seg_kind == kSeg16 ? 2 : 4);
+  gd->seg.alloc(seg_bytes);
+  launch_build_segments(N, gd->row_ptr.p, gd->col.p, gd->packed ? nullptr : gd->delay.p,
+                        gd->shift, gd->max_delay, gd->seg.p, gd->seg_kind, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
   if (gd->packed) gd->delay.reset();
   return gd;
 }
@@ -221,7 +232,7 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   // layout
   int64_t tiles = 0;
   int32_t rbase = 0;
-  uint64_t list_cap = 0;
+  int32_t dmax_all = 1;
   for (int k = 0; k < n; ++k) {
     const InstSpec& sp = specs[k];
     InstHost& ih = inst[k];
@@ -232,18 +243,13 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     tiles += ih.n_tiles;
     ih.rbase = rbase;
     rbase += g.R;
-    int min_nref = 255;
-    for (int32_t r = 0; r < g.R; ++r) {
+    for (int32_t r = 0; r < g.R; ++r)
       ih.rc_h.push_back(region_const(sp.params[r], sp.opt.dt_ms, S, g.ro_h[r], g.ro_h[r + 1],
                                      g.ro_h[r] + g.nexc_h[r]));
-      min_nref = std::min(min_nref, (int)ih.rc_h.back().n_ref);
-    }
-    const uint64_t per = (uint64_t)((g.max_delay + min_nref) / (min_nref + 1));
-    list_cap += (uint64_t)g.N * std::max<uint64_t>(per, 1);
+    dmax_all = std::max(dmax_all, g.max_delay);
     ih.opt = sp.opt;
     ih.net_id = sp.net_id;
   }
-  list_cap = std::min<uint64_t>(std::max<uint64_t>(list_cap, 1024), uint64_t(1) << 28);
   n_tiles = (int32_t)tiles;
   total_R = rbase;
   stride = tiles * kTile;
@@ -256,12 +262,19 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
   CK(cudaMemsetAsync(ref.p, 0, stride, stream));
   CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * stride, stream));
-  std::vector<int32_t> tile_inst_h((size_t)tiles), region_inst_h((size_t)total_R);
+  std::vector<int4> tile_info_h((size_t)tiles);
+  std::vector<int32_t> region_inst_h((size_t)total_R);
   std::vector<InstDesc> desc_h((size_t)n);
   for (int k = 0; k < n; ++k) {
     InstHost& ih = inst[k];
     const GraphDev& g = *ih.graph;
-    for (int t = 0; t < ih.n_tiles; ++t) tile_inst_h[(size_t)(ih.first_tile + t)] = k;
+    for (int t = 0; t < ih.n_tiles; ++t) {
+      // regions touched by the tile's neurons [t*kTile, min((t+1)*kTile, N))
+      const int32_t lo = t * kTile, hi = std::min((t + 1) * kTile, g.N) - 1;
+      const int32_t r0 = (int32_t)(std::upper_bound(g.ro_h.begin(), g.ro_h.end(), lo) - g.ro_h.begin()) - 1;
+      const int32_t r1 = (int32_t)(std::upper_bound(g.ro_h.begin(), g.ro_h.end(), hi) - g.ro_h.begin()) - 1;
+      tile_info_h[(size_t)(ih.first_tile + t)] = make_int4(k, r0, r1 - r0 + 1, 0);
+    }
     for (int32_t r = 0; r < g.R; ++r) region_inst_h[(size_t)(ih.rbase + r)] = k;
     ih.rc.alloc(g.R);
     CK(cudaMemcpyAsync(ih.rc.p, ih.rc_h.data(), sizeof(RegionConst) * g.R, cudaMemcpyHostToDevice, stream));
@@ -277,6 +290,9 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     d.col = g.col.p;
     d.w = g.w.p;
     d.delay = g.packed ? nullptr : g.delay.p;
+    d.seg = g.seg.p;
+    d.seg_kind = g.seg_kind;
+    d.dmax = g.max_delay;
     d.region_offsets = g.ro.p;
     d.rc = ih.rc.p;
     d.bold = ih.bold.p;
@@ -308,16 +324,18 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   }
   desc.alloc(n);
   dyn.alloc(n);
-  tile_inst.alloc(std::max<int64_t>(tiles, 1));
+  tile_info.alloc(std::max<int64_t>(tiles, 1));
+  closed.alloc(std::max(total_R, 1));
   region_inst.alloc(std::max(total_R, 1));
   cnt.alloc(std::max(total_R, 1));
   bw.alloc(4 * std::max(total_R, 1));
   ylast.alloc(std::max(total_R, 1));
-  list0.alloc(list_cap);
-  list1.alloc(list_cap);
-  count.alloc(2);
-  iter.alloc(1);
-  done.alloc(1);
+  // spike ring: a slot per step of the longest delay, each able to hold every neuron
+  const int32_t D = dmax_all + 1;
+  if (stride >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "too many neurons in one engine");
+  hist.alloc((int64_t)D * stride);
+  hcount.alloc(D);
+  base.alloc(2);
   events.alloc(1);
   flags.alloc(1);
   std::vector<InstDyn> dyn_h((size_t)n);
@@ -332,14 +350,14 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   }
   CK(cudaMemcpyAsync(desc.p, desc_h.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(dyn.p, dyn_h.data(), sizeof(InstDyn) * n, cudaMemcpyHostToDevice, stream));
-  CK(cudaMemcpyAsync(tile_inst.p, tile_inst_h.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(tile_info.p, tile_info_h.data(), sizeof(int4) * tiles, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(closed.p, 0, sizeof(long long) * std::max(total_R, 1), stream));
   CK(cudaMemcpyAsync(region_inst.p, region_inst_h.data(), sizeof(int32_t) * total_R, cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(total_R, 1), stream));
   CK(cudaMemcpyAsync(bw.p, bw_h.data(), sizeof(double) * 4 * total_R, cudaMemcpyHostToDevice, stream));
   CK(cudaMemsetAsync(ylast.p, 0, sizeof(double) * std::max(total_R, 1), stream));
-  CK(cudaMemsetAsync(count.p, 0, sizeof(uint32_t) * 2, stream));
-  CK(cudaMemsetAsync(iter.p, 0, sizeof(unsigned long long), stream));
-  CK(cudaMemsetAsync(done.p, 0, sizeof(unsigned), stream));
+  CK(cudaMemsetAsync(hcount.p, 0, sizeof(uint32_t) * D, stream));
+  CK(cudaMemsetAsync(base.p, 0, sizeof(unsigned long long) * 2, stream));
   CK(cudaMemsetAsync(events.p, 0, sizeof(unsigned long long), stream));
   CK(cudaMemsetAsync(flags.p, 0, sizeof(unsigned), stream));
 
@@ -351,19 +369,18 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   dev.stride = stride;
   dev.insts = desc.p;
   dev.dyn = dyn.p;
-  dev.tile_inst = tile_inst.p;
+  dev.tile_info = tile_info.p;
+  dev.closed = closed.p;
   dev.cnt = cnt.p;
   dev.bw = bw.p;
   dev.ylast = ylast.p;
   dev.region_inst = region_inst.p;
-  dev.list0 = list0.p;
-  dev.list1 = list1.p;
-  dev.count = count.p;
-  dev.iter = iter.p;
-  dev.done = done.p;
+  dev.hist = hist.p;
+  dev.hcount = hcount.p;
+  dev.hist_cap = stride;
+  dev.D = D;
   dev.events = events.p;
   dev.flags = flags.p;
-  dev.list_cap = list_cap;
   dev.n_inst = n;
   dev.n_tiles = n_tiles;
   dev.total_R = total_R;
@@ -387,12 +404,19 @@ void Engine::check() const {
   if (poisoned) raise(DBNET_ESTATE, "handle poisoned by an earlier failure: " + poison_msg);
 }
 
+// kChunk steps in two halves: the first half finds its iteration at
+// base[0] + i and its last update writes base[1]; the second half reads
+// base[1] and its last update writes base[0] for the next replay.
 void Engine::capture() {
   cudaGraph_t g = nullptr;
+  constexpr int half = kChunk / 2;
   CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < kChunk; ++i) {
-    launch_deliver(dev, del_grid, stream);
-    launch_update(dev, stream);
+    const int h = i / half, off = i % half;
+    const StepRef rd{base.p + h, (unsigned long long)off, nullptr};
+    const StepRef ru{base.p + h, (unsigned long long)off, off == half - 1 ? base.p + (1 - h) : nullptr};
+    launch_deliver(dev, del_grid, rd, stream);
+    launch_update(dev, ru, stream);
   }
   cudaError_t e1 = cudaStreamEndCapture(stream, &g);
   if (e1 != cudaSuccess) raise(DBNET_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
@@ -404,15 +428,22 @@ void Engine::capture() {
 void Engine::step(int64_t n) {
   check();
   if (n < 0) raise(DBNET_EINVAL, "n_steps must be >= 0");
-  if (n >= kChunk && !gexec) capture();
-  while (n >= kChunk) {
-    CK(cudaGraphLaunch(gexec, stream));
-    n -= kChunk;
+  if (n == 0) return;
+  if (n >= kChunk) {
+    if (!gexec) capture();
+    launch_set_base(base.p, g_host, stream);
+    while (n >= kChunk) {
+      CK(cudaGraphLaunch(gexec, stream));
+      n -= kChunk;
+      g_host += kChunk;
+    }
   }
-  for (; n > 0; --n) {
-    launch_deliver(dev, del_grid, stream);
-    launch_update(dev, stream);
+  for (; n > 0; --n, ++g_host) {
+    const StepRef sr{nullptr, g_host, nullptr};
+    launch_deliver(dev, del_grid, sr, stream);
+    launch_update(dev, sr, stream);
   }
+  launch_close(dev, g_host, stream);
   CK(cudaGetLastError());
 }
 
@@ -426,11 +457,12 @@ void Engine::step_timed(int64_t n, double* ms) {
   try {
     while (n > 0) {
       const int b = (int)std::min<int64_t>(n, kPool);
-      for (int i = 0; i < b; ++i) {
+      for (int i = 0; i < b; ++i, ++g_host) {
+        const StepRef sr{nullptr, g_host, nullptr};
         CK(cudaEventRecord(ev[3 * i], stream));
-        launch_deliver(dev, del_grid, stream);
+        launch_deliver(dev, del_grid, sr, stream);
         CK(cudaEventRecord(ev[3 * i + 1], stream));
-        launch_update(dev, stream);
+        launch_update(dev, sr, stream);
         CK(cudaEventRecord(ev[3 * i + 2], stream));
       }
       CK(cudaGetLastError());
@@ -449,6 +481,8 @@ void Engine::step_timed(int64_t n, double* ms) {
     throw;
   }
   for (auto& x : ev) cudaEventDestroy(x);
+  launch_close(dev, g_host, stream);
+  CK(cudaGetLastError());
   ms[0] = t_del;
   ms[1] = t_upd;
 }
@@ -458,8 +492,14 @@ void Engine::sync() {
   CK(cudaStreamSynchronize(stream));
   unsigned f = 0;
   CK(cudaMemcpy(&f, flags.p, sizeof(f), cudaMemcpyDeviceToHost));
-  if (f & kFlagListOverflow)
-    raise(DBNET_ERANGE, "live delivery list overflowed its capacity");
+  if (f & kFlagHistOverflow)
+    raise(DBNET_ERANGE, "spike ring overflowed its capacity");
+}
+
+int64_t Engine::bold_samples(int k) const {
+  const InstDesc& d = inst[k].desc;
+  const int64_t steps = (int64_t)(g_host - d.g0);
+  return steps / d.spb / d.bins_per_tr;
 }
 
 InstDyn Engine::read_dyn(int k) {
@@ -621,7 +661,8 @@ int dbnet_read_bold(dbnet_t* h, double* y, int64_t cap_samples, int64_t* n_out) 
     Engine& e = *h->eng;
     const InstHost& ih = e.inst[h->inst];
     InstDyn d = e.read_dyn(h->inst);
-    const int64_t avail = std::min<int64_t>(d.bold_count, ih.opt.bold_capacity);
+    (void)d;
+    const int64_t avail = std::min<int64_t>(e.bold_samples(h->inst), ih.opt.bold_capacity);
     const int64_t n = std::min(avail, cap_samples);
     if (n > 0)
       CK(cudaMemcpy(y, ih.bold.p, sizeof(double) * n * ih.graph->R, cudaMemcpyDeviceToHost));
@@ -694,13 +735,13 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     unsigned long long ev = 0;
     CK(cudaMemcpy(&ev, e.events.p, sizeof(ev), cudaMemcpyDeviceToHost));
     std::memset(out, 0, sizeof(*out));
-    out->step = d.step;
+    out->step = (int64_t)(e.g_host - ih.desc.g0);
     out->spikes = (int64_t)d.spikes;
     out->events = (int64_t)ev;
     const int64_t cap = ih.opt.raster_capacity;
     out->raster_len = std::min<int64_t>((int64_t)d.raster_count, cap);
     out->raster_dropped = std::max<int64_t>((int64_t)d.raster_count - cap, 0);
-    out->bold_samples = std::min<int64_t>(d.bold_count, ih.opt.bold_capacity);
+    out->bold_samples = std::min<int64_t>(e.bold_samples(h->inst), ih.opt.bold_capacity);
     out->fixed_shift = e.shift_S;
     out->max_delay = ih.graph->max_delay;
     out->packed_edges = ih.graph->packed ? 1 : 0;

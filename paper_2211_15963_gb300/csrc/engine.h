@@ -13,9 +13,15 @@
 // Edges of an instance (CSR by source, rows sorted by delay):
 //   col[e] u32 = target | delay << shift  (or target, with delay[e] u8)
 //   w[e]   u16 BF16 bit pattern
-// Live delivery list: one 16-byte entry per spike whose later-delay edges are
-// still to be delivered (position in the row, current delay, class, rows left,
-// instance).
+//   seg[j][k] u16/u32 = number of edges of row j with delay <= k + 1,
+//                       k < dmax (the per-delay segment table)
+// Iteration g of an engine runs k_deliver then k_update; the bin that ends
+// with iteration g - 1 is closed (Balloon-Windkessel step, BOLD sample) at
+// the start of k_deliver(g), one region per thread.
+// Spike ring: D slots; slot n mod D lists the spikes of step n as
+//   global index | class << 31, with a count per slot.  At step n the
+//   delivery reads slots n - d (d = 1..D-1) and applies, for each listed
+//   spike, the segment of its row whose delay is exactly d.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,6 +34,8 @@ constexpr int kTile = 1024;         // neurons per update block
 constexpr int kUpdThreads = 256;    // four neurons per thread
 constexpr int kDelThreads = 256;
 constexpr int kMaxThr = 16;         // Poisson inversion thresholds
+constexpr int kTileRegions = 8;     // region constants staged in shared memory
+constexpr int kLongSeg = 48;        // segments longer than this are shared by a warp
 
 struct RegionConst {
   float dtC, gL, VL, Vth, Vreset, Iext;
@@ -37,11 +45,18 @@ struct RegionConst {
   uint32_t thr[kMaxThr];
 };
 
+enum : int32_t {
+  kSegSearch = 0,  // no table: binary search over the row's delays
+  kSeg16 = 1,
+  kSeg32 = 2,
+};
+
 struct InstDesc {
   const int64_t* row_ptr;
   const uint32_t* col;
   const uint16_t* w;
   const uint8_t* delay;          // nullptr when the delay is packed into col
+  const void* seg;               // [N][dmax] segment table, or nullptr
   const int32_t* region_offsets; // [R+1], local
   const RegionConst* rc;         // [R]
   double* bold;                  // [bold_cap][R]
@@ -51,32 +66,34 @@ struct InstDesc {
   int64_t raster_cap;
   int64_t bold_cap;
   uint64_t seed, net_id;
+  unsigned long long g0;         // engine iteration at which this instance's step 0 ran
   int32_t N, R, rbase, shift;
   uint32_t tmask;
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;
-  int32_t pad;
+  int32_t seg_kind, dmax;
   double h_bw, z_scale, kappa, gamma, tau, alpha, rho, V0;
 };
 
 struct InstDyn {
-  long long step;
-  long long bins_done;
-  long long bold_count;
   unsigned long long raster_count;
   unsigned long long spikes;
   int32_t active;
   int32_t pad;
 };
 
-struct __align__(16) Entry {
-  unsigned long long pdc;  // position (48 bits) | delay done (8) | class (8)
-  uint32_t rem;            // edges of the row not yet delivered
-  uint32_t inst;
+// Where a kernel finds its engine iteration g: *base + off, or off when base
+// is null (direct launches).  When next is set, the kernel also writes g + 1
+// there (every block writes the same value), which lets a captured graph
+// chain its halves through two base words.
+struct StepRef {
+  const unsigned long long* base;
+  unsigned long long off;
+  unsigned long long* next;
 };
 
 enum : unsigned {
-  kFlagListOverflow = 1u,
+  kFlagHistOverflow = 1u,
   kFlagBoldOverflow = 2u,
 };
 
@@ -88,33 +105,38 @@ struct EngineDev {
   int64_t stride;
   const InstDesc* insts;
   InstDyn* dyn;
-  const int32_t* tile_inst;
+  const int4* tile_info;  // per tile: instance, first region (local), regions touched, 0
   int32_t* cnt;          // [total_R] spikes in the current bin
   double* bw;            // [total_R][4]
   double* ylast;         // [total_R]
   const int32_t* region_inst;
-  Entry* list0;
-  Entry* list1;
-  uint32_t* count;       // [2]
-  unsigned long long* iter;
-  unsigned int* done;
+  long long* closed;     // [total_R] last iteration whose bin was closed
+  uint32_t* hist;        // [D][hist_cap]
+  uint32_t* hcount;      // [D]
+  int64_t hist_cap;
   unsigned long long* events;
   unsigned int* flags;
-  uint64_t list_cap;
-  int32_t n_inst, n_tiles, total_R, pad;
+  int32_t D;
+  int32_t n_inst, n_tiles, total_R;
 };
 
 // Launchers (kernels.cu)
 void launch_init_state(const EngineDev& e, int inst, int n_tiles_inst, int first_tile,
                        cudaStream_t s);
-void launch_update(const EngineDev& e, cudaStream_t s);
-void launch_deliver(const EngineDev& e, int grid, cudaStream_t s);
+void launch_update(const EngineDev& e, StepRef sr, cudaStream_t s);
+void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s);
+// closes the bin that ends with iteration g - 1 (if any) for every region
+void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s);
+void launch_set_base(unsigned long long* base, unsigned long long g, cudaStream_t s);
 int deliver_grid();
 void launch_validate_pack(int32_t N, const int64_t* row_ptr, uint32_t* col, const void* w_in,
                           int32_t w_dtype, uint16_t* w_out, const uint8_t* delay_in,
                           int32_t shift, int32_t* indeg, unsigned* wmax_bits,
                           unsigned* dmax, unsigned* err, cudaStream_t s);
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s);
+void launch_build_segments(int32_t N, const int64_t* row_ptr, const uint32_t* col,
+                           const uint8_t* delay, int32_t shift, int32_t dmax, void* seg,
+                           int32_t seg_kind, cudaStream_t s);
 
 enum : unsigned {
   kErrTarget = 1u,

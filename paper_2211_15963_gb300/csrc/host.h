@@ -73,6 +73,8 @@ struct GraphDev {
   DevBuf<uint16_t> w;
   DevBuf<uint8_t> delay;
   DevBuf<int32_t> ro;
+  DevBuf<uint8_t> seg;  // [N][max_delay] u16 or u32 segment table
+  int32_t seg_kind = 0;
   int32_t shift = 32;
   uint32_t tmask = 0xFFFFFFFFu;
   bool packed = false;
@@ -110,12 +112,14 @@ struct Engine {
   DevBuf<int2> acc;
   DevBuf<InstDesc> desc;
   DevBuf<InstDyn> dyn;
-  DevBuf<int32_t> tile_inst, region_inst, cnt;
+  DevBuf<int4> tile_info;
+  DevBuf<int32_t> region_inst, cnt;
+  DevBuf<long long> closed;
   DevBuf<double> bw, ylast;
-  DevBuf<Entry> list0, list1;
-  DevBuf<uint32_t> count;
-  DevBuf<unsigned long long> iter, events;
-  DevBuf<unsigned> done, flags;
+  DevBuf<uint32_t> hist, hcount;
+  DevBuf<unsigned long long> base, events;  // base: the two graph-half iteration words
+  DevBuf<unsigned> flags;
+  unsigned long long g_host = 0;            // iterations enqueued so far
   EngineDev dev{};
   cudaGraphExec_t gexec = nullptr;
   int del_grid = 0;
@@ -134,6 +138,7 @@ struct Engine {
   void step_timed(int64_t n, double* ms);
   void sync();
   InstDyn read_dyn(int k);
+  int64_t bold_samples(int k) const;
 };
 
 std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s);

@@ -3,16 +3,22 @@
 //   k_update   one Euler step of every neuron (Methods, capacitance-voltage
 //              equation and Eq. 2; Supplementary Sec. 3, Eqs. 3 and 5 with
 //              the refractory reset), the Poisson background drawn from
-//              Philox4x64-10, spike compaction into the live delivery list,
-//              region spike counts, and -- in the block that finishes last --
-//              the per-bin Balloon-Windkessel step (Extended Data Table 4).
-//   k_deliver  push delivery (Supplementary Algorithm 2) at arrival time: each
-//              live entry applies the out-edges of its spike whose delay has
-//              come due to the fixed-point accumulators of this step, then
-//              survives if later delays remain.
+//              Philox4x64-10, spike compaction into the spike ring,
+//              and region spike counts.
+//   k_close / the head of k_deliver: the per-bin Balloon-Windkessel step
+//              (Extended Data Table 4) and the BOLD sample, one region per
+//              thread.
+//   k_deliver  push delivery (Supplementary Algorithm 2) at arrival time: for
+//              every spike of step n - d (d = 1..D-1, from the spike ring)
+//              the edges of its row with delay exactly d -- one contiguous
+//              segment found in the per-delay segment table -- are added to
+//              this step's fixed-point accumulators.
 //
-// Both kernels read the step index and list parity from device memory, so a
-// captured CUDA graph of (deliver, update) pairs is valid for any step.
+// Both kernels find their iteration through a StepRef (a base word in device
+// memory plus an offset), so a captured CUDA graph of (deliver, update) pairs
+// is valid for any step.  The bin that ends with an iteration is closed (BW
+// step, BOLD sample) by the next k_deliver, or by k_close at the end of a
+// step call.
 //
 // The FP32 neuron arithmetic is written with explicit round-to-nearest
 // intrinsics in a fixed order so that no operation is fused or reordered; the
@@ -103,35 +109,84 @@ __global__ void __launch_bounds__(kUpdThreads) k_init_state(EngineDev e, int ins
   *reinterpret_cast<int4*>(e.acc + gi0 + 2) = make_int4(0, 0, 0, 0);
 }
 
-__global__ void __launch_bounds__(kUpdThreads) k_update(EngineDev e) {
-  __shared__ int s_last;
-  const int tile = blockIdx.x;
-  const int inst = e.tile_inst[tile];
-  const InstDesc& d = e.insts[inst];
-  const unsigned long long g = *reinterpret_cast<volatile unsigned long long*>(e.iter);
-  const long long n = e.dyn[inst].step;
-  const bool active = e.dyn[inst].active != 0;
-  const int lane = threadIdx.x & 31;
-  Entry* out_list = (g & 1ull) ? e.list0 : e.list1;
-  uint32_t* out_count = &e.count[(g + 1ull) & 1ull];
+__device__ __forceinline__ unsigned long long step_of(const StepRef& sr) {
+  return (sr.base ? *reinterpret_cast<const volatile unsigned long long*>(sr.base) : 0ull) + sr.off;
+}
 
+// Close the bin that ended with iteration g - 1 for region gr, once: the
+// Balloon-Windkessel step with that bin's activity, and the BOLD sample when
+// the bin ends a TR.
+__device__ void close_region(const EngineDev& e, int gr, unsigned long long g) {
+  const int k = e.region_inst[gr];
+  if (!e.dyn[k].active) return;
+  const InstDesc& dk = e.insts[k];
+  if (g <= dk.g0) return;
+  const long long nk = (long long)(g - 1ull - dk.g0);  // step just completed
+  if ((nk + 1) % dk.spb != 0) return;
+  if (e.closed[gr] >= (long long)g) return;
+  const int r = gr - dk.rbase;
+  const double nr = (double)(dk.rc[r].end - dk.rc[r].start);
+  const double z = dk.z_scale * (double)e.cnt[gr] / nr;
+  e.cnt[gr] = 0;
+  const double y = bw_euler(e.bw + 4 * gr, z, dk);
+  e.ylast[gr] = y;
+  const long long b = (nk + 1) / dk.spb;  // bins completed
+  if (b % dk.bins_per_tr == 0) {
+    const long long sidx = b / dk.bins_per_tr - 1;
+    if (sidx < dk.bold_cap) dk.bold[sidx * dk.R + r] = y;
+  }
+  e.closed[gr] = (long long)g;
+}
+
+__global__ void k_close(EngineDev e, unsigned long long g) {
+  for (int gr = blockIdx.x * blockDim.x + threadIdx.x; gr < e.total_R; gr += gridDim.x * blockDim.x)
+    close_region(e, gr, g);
+}
+
+__global__ void k_set_base(unsigned long long* base, unsigned long long g) { *base = g; }
+
+__global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef sr) {
+  __shared__ RegionConst s_rc[kTileRegions];
+  __shared__ uint32_t s_wtot[kUpdThreads / 32];
+  __shared__ uint32_t s_hbase;
+  __shared__ unsigned long long s_rbase;
+  const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // state loads first: they depend only on the tile, and the arrays cover
+  // every padded tile
   const int64_t gi0 = (int64_t)tile * kTile + threadIdx.x * 4;
+  const float4 V4 = *reinterpret_cast<const float4*>(e.V + gi0);
+  float4 J4[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) J4[u] = *reinterpret_cast<const float4*>(e.J + u * e.stride + gi0);
+  const uchar4 rf = *reinterpret_cast<const uchar4*>(e.ref + gi0);
+  const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
+  const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
+
+  const int4 ti = e.tile_info[tile];  // instance, first region, regions touched
+  const int inst = ti.x, r0 = ti.y, nr = ti.z;
+  const InstDesc& d = e.insts[inst];
+  const unsigned long long g = step_of(sr);
+  if (sr.next && threadIdx.x == 0) *sr.next = g + 1ull;
+  const long long n = (long long)(g - d.g0);
+  const bool active = e.dyn[inst].active != 0;
+  if (nr <= kTileRegions) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(d.rc + r0);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_rc);
+    const int words = nr * (int)(sizeof(RegionConst) / 4);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  const RegionConst* rcp = nr <= kTileRegions ? s_rc : d.rc + r0;
+
   const int32_t li0 = (int32_t)(gi0 - d.base);
   unsigned spk = 0;       // bit k: neuron li0 + k spiked
   unsigned cls_bits = 0;  // bit k: that neuron is inhibitory
   int reg[4] = {0, 0, 0, 0};
 
   if (active && li0 < d.N) {
-    float4 V4 = *reinterpret_cast<const float4*>(e.V + gi0);
-    float4 J4[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) J4[u] = *reinterpret_cast<const float4*>(e.J + u * e.stride + gi0);
-    uchar4 rf = *reinterpret_cast<const uchar4*>(e.ref + gi0);
-    int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
-    int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
     *reinterpret_cast<int4*>(e.acc + gi0) = make_int4(0, 0, 0, 0);
     *reinterpret_cast<int4*>(e.acc + gi0 + 2) = make_int4(0, 0, 0, 0);
-
     unsigned long long x[4] = {(unsigned long long)n, (unsigned long long)(li0 >> 2), 0ull, 0ull};
     philox4x64_10(x, d.seed, d.net_id);
 
@@ -141,16 +196,16 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(EngineDev e) {
                      {J4[2].x, J4[2].y, J4[2].z, J4[2].w},
                      {J4[3].x, J4[3].y, J4[3].z, J4[3].w}};
     int rr[4] = {rf.x, rf.y, rf.z, rf.w};
-    int aE[4] = {a01.x, a01.z, a23.x, a23.z};
-    int aI[4] = {a01.y, a01.w, a23.y, a23.w};
-    int r = find_region(d.region_offsets, d.R, li0);
+    const int aE[4] = {a01.x, a01.z, a23.x, a23.z};
+    const int aI[4] = {a01.y, a01.w, a23.y, a23.w};
+    int r = 0;  // relative to r0
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int32_t li = li0 + k;
       if (li >= d.N) break;
-      while (li >= d.rc[r].end) ++r;
-      reg[k] = r;
-      const RegionConst& p = d.rc[r];
+      while (li >= rcp[r].end) ++r;
+      reg[k] = r0 + r;
+      const RegionConst& p = rcp[r];
       // background: Poisson count by integer inversion of 32 Philox bits
       const uint32_t uu = (uint32_t)(x[k] >> 32);
       int c = 0;
@@ -199,198 +254,245 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(EngineDev e) {
                     (unsigned char)rr[3]);
   }
 
-  // ---- spikes: live-list entries, raster, region and spike counts ----------
-  const unsigned any = __ballot_sync(kFull, spk != 0);
-  if (any) {
-    int64_t rs[4], re[4];
-    int n_app = 0;
+  // ---- spikes: one ring append, spike and raster count per block ---------
+  if (!__syncthreads_or(spk != 0)) return;
+  const int nsp = __popc(spk);
+  int ps = nsp;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      rs[k] = re[k] = 0;
-      if (spk & (1u << k)) {
-        rs[k] = __ldg(d.row_ptr + li0 + k);
-        re[k] = __ldg(d.row_ptr + li0 + k + 1);
-        if (re[k] > rs[k]) ++n_app;
-        atomicAdd(&e.cnt[d.rbase + reg[k]], 1);
-      }
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, ps, o);
+    if (lane >= o) ps += t;
+  }
+  if (lane == 31) s_wtot[warp] = (uint32_t)ps;
+  __syncthreads();
+  const int slot = (int)(g % (unsigned long long)e.D);
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < kUpdThreads / 32; ++w) {
+      const uint32_t c = s_wtot[w];
+      s_wtot[w] = tot;  // exclusive prefix
+      tot += c;
     }
-    const int n_spk = __popc(spk);
-    // warp-level exclusive scans
-    int pa = n_app, ps = n_spk;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int ta = __shfl_up_sync(kFull, pa, o), ts = __shfl_up_sync(kFull, ps, o);
-      if (lane >= o) { pa += ta; ps += ts; }
-    }
-    const int tot_a = __shfl_sync(kFull, pa, 31), tot_s = __shfl_sync(kFull, ps, 31);
-    unsigned long long base_a = 0, base_s = 0;
-    if (lane == 0) {
-      if (tot_a) base_a = atomicAdd(out_count, (uint32_t)tot_a);
-      base_s = atomicAdd(&e.dyn[inst].spikes, (unsigned long long)tot_s);
-      if (d.raster_cap > 0) base_s = atomicAdd(&e.dyn[inst].raster_count, (unsigned long long)tot_s);
-    }
-    base_a = __shfl_sync(kFull, base_a, 0) + (unsigned long long)(pa - n_app);
-    base_s = __shfl_sync(kFull, base_s, 0) + (unsigned long long)(ps - n_spk);
+    s_hbase = atomicAdd(e.hcount + slot, tot);
+    atomicAdd(&e.dyn[inst].spikes, (unsigned long long)tot);
+    s_rbase = d.raster_cap > 0 ? atomicAdd(&e.dyn[inst].raster_count, (unsigned long long)tot) : 0ull;
+  }
+  __syncthreads();
+  if (spk) {
+    uint64_t pos = (uint64_t)s_hbase + s_wtot[warp] + (uint32_t)(ps - nsp);
+    unsigned long long rpos = s_rbase + s_wtot[warp] + (unsigned long long)(ps - nsp);
+    uint32_t* hslot = e.hist + (size_t)slot * (size_t)e.hist_cap;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (!(spk & (1u << k))) continue;
-      if (re[k] > rs[k]) {
-        if (base_a < e.list_cap) {
-          Entry en;
-          en.pdc = (unsigned long long)rs[k] | ((unsigned long long)((cls_bits >> k) & 1u) << 56);
-          en.rem = (uint32_t)(re[k] - rs[k]);
-          en.inst = (uint32_t)inst;
-          out_list[base_a] = en;
-        } else {
-          atomicOr(e.flags, kFlagListOverflow);
-        }
-        ++base_a;
-      }
+      if (pos < (uint64_t)e.hist_cap)
+        hslot[pos] = (uint32_t)(gi0 + k) | (((cls_bits >> k) & 1u) << 31);
+      else
+        atomicOr(e.flags, kFlagHistOverflow);
+      ++pos;
+      atomicAdd(&e.cnt[d.rbase + reg[k]], 1);
       if (d.raster_cap > 0) {
-        if (base_s < (unsigned long long)d.raster_cap) {
-          d.raster_step[base_s] = (int32_t)n;
-          d.raster_id[base_s] = li0 + k;
+        if (rpos < (unsigned long long)d.raster_cap) {
+          d.raster_step[rpos] = (int32_t)n;
+          d.raster_id[rpos] = li0 + k;
         }
-        ++base_s;
+        ++rpos;
       }
     }
-  }
-
-  // ---- the last block to finish closes the step ---------------------------
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(e.done, 1u);
-    s_last = (t == gridDim.x - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // per-bin hemodynamic step for every region of every active instance
-  for (int gr = threadIdx.x; gr < e.total_R; gr += blockDim.x) {
-    const int k = e.region_inst[gr];
-    if (!e.dyn[k].active) continue;
-    const InstDesc& dk = e.insts[k];
-    const long long nk = e.dyn[k].step;
-    if ((nk + 1) % dk.spb != 0) continue;
-    const int r = gr - dk.rbase;
-    const double nr = (double)(dk.rc[r].end - dk.rc[r].start);
-    volatile int* cp = e.cnt + gr;
-    const double z = dk.z_scale * (double)(*cp) / nr;
-    *cp = 0;
-    const double y = bw_euler(e.bw + 4 * gr, z, dk);
-    e.ylast[gr] = y;
-    const long long b = e.dyn[k].bins_done + 1;
-    if (b % dk.bins_per_tr == 0) {
-      const long long sidx = e.dyn[k].bold_count;
-      if (sidx < dk.bold_cap) dk.bold[sidx * dk.R + r] = y;
-    }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < e.n_inst; k += blockDim.x) {
-    if (!e.dyn[k].active) continue;
-    const InstDesc& dk = e.insts[k];
-    const long long nk = e.dyn[k].step;
-    if ((nk + 1) % dk.spb == 0) {
-      const long long b = e.dyn[k].bins_done + 1;
-      e.dyn[k].bins_done = b;
-      if (b % dk.bins_per_tr == 0) {
-        if (e.dyn[k].bold_count >= dk.bold_cap) atomicOr(e.flags, kFlagBoldOverflow);
-        e.dyn[k].bold_count += 1;
-      }
-    }
-    e.dyn[k].step = nk + 1;
-  }
-  if (threadIdx.x == 0) {
-    e.count[g & 1ull] = 0u;  // that list was consumed by this step's delivery
-    *e.done = 0u;
-    __threadfence();
-    *e.iter = g + 1ull;
   }
 }
 
-__global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e) {
-  const unsigned long long g = *reinterpret_cast<volatile unsigned long long*>(e.iter);
-  const int cur = (int)(g & 1ull);
-  const unsigned long long n_cnt = e.count[cur];
-  const uint32_t n_in =
-      (uint32_t)(n_cnt < (unsigned long long)e.list_cap ? n_cnt : (unsigned long long)e.list_cap);
-  const Entry* __restrict__ in = cur ? e.list1 : e.list0;
-  Entry* __restrict__ out = cur ? e.list0 : e.list1;
-  uint32_t* n_out = &e.count[cur ^ 1];
-  const int lane = threadIdx.x & 31;
-  unsigned long long ev = 0;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t b0 = blockIdx.x * blockDim.x; b0 < n_in; b0 += stride) {
-    const uint32_t idx = b0 + threadIdx.x;
-    bool keep = false;
-    Entry en;
-    if (idx < n_in) {
-      en = in[idx];
-      const InstDesc& d = e.insts[en.inst];
-      unsigned long long pos = en.pdc & 0xFFFFFFFFFFFFull;
-      const uint32_t due = (uint32_t)((en.pdc >> 48) & 0xFFull) + 1u;
-      const uint32_t cls = (uint32_t)(en.pdc >> 56);
-      uint32_t rem = en.rem;
-      const uint32_t* __restrict__ col = d.col;
-      const uint16_t* __restrict__ w = d.w;
-      const uint8_t* __restrict__ dl = d.delay;
-      const int shift = d.shift;
-      const uint32_t tmask = d.tmask;
-      const float two_S = d.two_S;
-      int* accp = reinterpret_cast<int*>(e.acc + d.base) + cls;
-      bool go = true;
-      while (go && rem > 0) {
-        // up to four edges loaded together, then applied in row order while
-        // their delay is the one due at this step
-        const uint32_t nb = rem < 4u ? rem : 4u;
-        uint32_t cc[4], dd[4];
-        uint16_t ww[4];
+__device__ __forceinline__ uint32_t edge_delay(const uint32_t* col, const uint8_t* dl, int shift,
+                                               int64_t e) {
+  return dl ? (uint32_t)__ldg(dl + e) : (__ldg(col + e) >> shift);
+}
+
+// first edge in [lo, hi) whose delay is >= d (rows are sorted by delay)
+__device__ int64_t first_delay_at_least(const uint32_t* col, const uint8_t* dl, int shift,
+                                        int64_t lo, int64_t hi, uint32_t d) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (edge_delay(col, dl, shift, mid) < d) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr) {
+  __shared__ unsigned long long s_pre[256];  // items whose delay is below index + 1
+  __shared__ unsigned long long s_wsum[kDelThreads / 32];
+  __shared__ unsigned long long s_total;
+  const unsigned long long g = step_of(sr);
+  const int D = e.D;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  // close the bin that ended with the previous iteration, one region per thread
+  for (int gr = gtid; gr < e.total_R; gr += gridDim.x * blockDim.x) close_region(e, gr, g);
+  // the slot this iteration's update will fill was last read by the previous one
+  if (gtid == 0) e.hcount[g % (unsigned long long)D] = 0u;
+
+  // spikes of step g - d for d = threadIdx.x + 1, and their exclusive prefix
+  unsigned long long c = 0;
+  const int dme = threadIdx.x + 1;
+  if (dme < D && g >= (unsigned long long)dme) {
+    const unsigned long long h = e.hcount[(g - dme) % (unsigned long long)D];
+    c = h < (unsigned long long)e.hist_cap ? h : (unsigned long long)e.hist_cap;
+  }
+  unsigned long long incl = c;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          cc[t] = 0u;
-          ww[t] = 0;
-          dd[t] = 0u;
-          if ((uint32_t)t < nb) {
-            cc[t] = __ldg(col + pos + t);
-            ww[t] = __ldg(w + pos + t);
-            dd[t] = dl ? (uint32_t)__ldg(dl + pos + t) : (cc[t] >> shift);
-          }
-        }
-        uint32_t taken = 0;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          go = go && (uint32_t)t < nb && dd[t] == due;
-          if (go) {
-            const uint32_t tgt = cc[t] & tmask;
-            const float wf = __uint_as_float((uint32_t)ww[t] << 16);
-            const int q = __float2int_rn(__fmul_rn(wf, two_S));
-            atomicAdd(accp + 2 * (size_t)tgt, q);
-            ++taken;
-          }
-        }
-        pos += taken;
-        rem -= taken;
-        ev += taken;
-      }
-      keep = rem > 0;
-      en.pdc = pos | ((unsigned long long)due << 48) | ((unsigned long long)cls << 56);
-      en.rem = rem;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long acc = 0;
+    for (int w = 0; w < kDelThreads / 32; ++w) {
+      const unsigned long long t = s_wsum[w];
+      s_wsum[w] = acc;
+      acc += t;
     }
-    const unsigned m = __ballot_sync(kFull, keep);
-    if (m) {
-      uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(n_out, (uint32_t)__popc(m));
-      base = __shfl_sync(kFull, base, 0) + (uint32_t)__popc(m & ((1u << lane) - 1u));
-      if (keep) {
-        if (base < e.list_cap) out[base] = en;
-        else atomicOr(e.flags, kFlagListOverflow);
+    s_total = acc;
+  }
+  __syncthreads();
+  s_pre[threadIdx.x] = s_wsum[warp] + incl - c;
+  const int nd = D - 1 < kDelThreads ? D - 1 : kDelThreads;  // delay buckets d = 1..nd
+  const unsigned long long W = s_total;
+  __syncthreads();
+
+  unsigned long long ev = 0;
+  const unsigned long long wstride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long wbase = (unsigned long long)blockIdx.x * blockDim.x + warp * 32;
+  for (unsigned long long b0 = wbase; b0 < W; b0 += wstride) {  // warp-uniform
+    const unsigned long long t = b0 + lane;
+    bool longseg = false;
+    int64_t e0 = 0;
+    uint32_t nseg = 0;
+    int inst = 0;
+    uint32_t cls = 0;
+    if (t < W) {
+      // bucket: the largest i with s_pre[i] <= t; delay d = i + 1
+      int lo = 0, hi = nd - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pre[mid] <= t) lo = mid; else hi = mid - 1;
       }
+      const uint32_t d = (uint32_t)lo + 1u;
+      const unsigned long long k = t - s_pre[lo];
+      const unsigned long long slot = (g - d) % (unsigned long long)D;
+      const uint32_t ent = e.hist[slot * (unsigned long long)e.hist_cap + k];
+      const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
+      cls = ent >> 31;
+      inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
+      const InstDesc& dd = e.insts[inst];
+      if ((int32_t)d <= dd.dmax) {
+        const int64_t j = gidx - dd.base;
+        const int64_t r0 = __ldg(dd.row_ptr + j);
+        int64_t a, b;
+        if (dd.seg_kind == kSeg16) {
+          const uint16_t* T = static_cast<const uint16_t*>(dd.seg) + j * dd.dmax;
+          a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
+          b = (int64_t)__ldg(T + d - 1);
+        } else if (dd.seg_kind == kSeg32) {
+          const uint32_t* T = static_cast<const uint32_t*>(dd.seg) + j * dd.dmax;
+          a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
+          b = (int64_t)__ldg(T + d - 1);
+        } else {
+          const int64_t r1 = __ldg(dd.row_ptr + j + 1);
+          a = first_delay_at_least(dd.col, dd.delay, dd.shift, r0, r1, d) - r0;
+          b = first_delay_at_least(dd.col, dd.delay, dd.shift, r0 + a, r1, d + 1) - r0;
+        }
+        nseg = (uint32_t)(b - a);
+        e0 = r0 + a;
+        longseg = nseg > (uint32_t)kLongSeg;
+        if (!longseg && nseg > 0) {
+          const uint32_t* __restrict__ col = dd.col;
+          const uint16_t* __restrict__ w = dd.w;
+          const uint32_t tmask = dd.tmask;
+          const float two_S = dd.two_S;
+          int* accp = reinterpret_cast<int*>(e.acc + dd.base) + cls;
+          for (uint32_t o = 0; o < nseg; o += 8) {
+            uint32_t cc[8];
+            uint16_t ww[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              cc[u] = 0u;
+              ww[u] = 0;
+              if (o + u < nseg) {
+                cc[u] = __ldg(col + e0 + o + u);
+                ww[u] = __ldg(w + e0 + o + u);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (o + u < nseg) {
+                const float wf = __uint_as_float((uint32_t)ww[u] << 16);
+                atomicAdd(accp + 2 * (size_t)(cc[u] & tmask), __float2int_rn(__fmul_rn(wf, two_S)));
+              }
+            }
+          }
+          ev += nseg;
+        }
+      }
+    }
+    // long segments of this warp, one at a time, all lanes (coalesced)
+    unsigned lm = __ballot_sync(kFull, longseg);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t q0 = __shfl_sync(kFull, e0, src);
+      const uint32_t qn = __shfl_sync(kFull, nseg, src);
+      const int qi = __shfl_sync(kFull, inst, src);
+      const uint32_t qc = __shfl_sync(kFull, cls, src);
+      const InstDesc& dd = e.insts[qi];
+      int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
+      for (uint32_t o = lane; o < qn; o += 32) {
+        const uint32_t cc = __ldg(dd.col + q0 + o);
+        const float wf = __uint_as_float((uint32_t)__ldg(dd.w + q0 + o) << 16);
+        atomicAdd(accp + 2 * (size_t)(cc & dd.tmask), __float2int_rn(__fmul_rn(wf, dd.two_S)));
+      }
+      if (lane == 0) ev += qn;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
-  if (lane == 0 && ev) atomicAdd(e.events, ev);
+  __syncthreads();
+  if (lane == 0) s_wsum[warp] = ev;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int w = 0; w < kDelThreads / 32; ++w) s += s_wsum[w];
+    if (s) atomicAdd(e.events, s);
+  }
+}
+
+// Segment table: seg[j][k] = number of edges of row j with delay <= k + 1.
+// Warp per row; every entry is written once.
+__global__ void k_build_segments(int32_t N, const int64_t* __restrict__ row_ptr,
+                                 const uint32_t* __restrict__ col, const uint8_t* __restrict__ dl,
+                                 int32_t shift, int32_t dmax, void* seg, int32_t kind) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < N; j += nwarps) {
+    const int64_t a = row_ptr[j], n = row_ptr[j + 1] - a;
+    uint16_t* T16 = static_cast<uint16_t*>(seg) + j * dmax;
+    uint32_t* T32 = static_cast<uint32_t*>(seg) + j * dmax;
+    auto put = [&](int k, uint32_t v) {
+      if (kind == kSeg16) T16[k] = (uint16_t)v; else T32[k] = v;
+    };
+    if (n == 0) {
+      for (int k = lane; k < dmax; k += 32) put(k, 0u);
+      continue;
+    }
+    for (int64_t p = lane; p < n; p += 32) {
+      const int dp = (int)edge_delay(col, dl, shift, a + p);
+      const int dn = p + 1 < n ? (int)edge_delay(col, dl, shift, a + p + 1) : dmax + 1;
+      if (p == 0)
+        for (int k = 0; k <= dp - 2; ++k) put(k, 0u);
+      for (int k = dp - 1; k <= dn - 2; ++k) put(k, (uint32_t)(p + 1));
+    }
+  }
 }
 
 // Validate and pack the edges of one graph: warp per source row.
@@ -468,8 +570,17 @@ void launch_init_state(const EngineDev& e, int inst, int n_tiles_inst, int first
   if (n_tiles_inst > 0) k_init_state<<<n_tiles_inst, kUpdThreads, 0, s>>>(e, inst, first_tile);
 }
 
-void launch_update(const EngineDev& e, cudaStream_t s) {
-  k_update<<<e.n_tiles, kUpdThreads, 0, s>>>(e);
+void launch_update(const EngineDev& e, StepRef sr, cudaStream_t s) {
+  k_update<<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+}
+
+void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s) {
+  const int blocks = (e.total_R + 127) / 128;
+  k_close<<<blocks > 0 ? blocks : 1, 128, 0, s>>>(e, g);
+}
+
+void launch_set_base(unsigned long long* base, unsigned long long g, cudaStream_t s) {
+  k_set_base<<<1, 1, 0, s>>>(base, g);
 }
 
 int deliver_grid() {
@@ -484,16 +595,15 @@ int deliver_grid() {
   return g_deliver_grid;
 }
 
-void launch_deliver(const EngineDev& e, int grid, cudaStream_t s) {
-  k_deliver<<<grid, kDelThreads, 0, s>>>(e);
+void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s) {
+  k_deliver<<<grid, kDelThreads, 0, s>>>(e, sr);
 }
 
 void launch_validate_pack(int32_t N, const int64_t* row_ptr, uint32_t* col, const void* w_in,
                           int32_t w_dtype, uint16_t* w_out, const uint8_t* delay_in,
                           int32_t shift, int32_t* indeg, unsigned* wmax_bits, unsigned* dmax,
                           unsigned* err, cudaStream_t s) {
-  int64_t warps = N;
-  int64_t blocks = (warps * 32 + 255) / 256;
+  int64_t blocks = ((int64_t)N * 32 + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
   k_validate_pack<<<(int)blocks, 256, 0, s>>>(N, row_ptr, col, w_in, w_dtype, w_out, delay_in,
@@ -505,6 +615,15 @@ void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t 
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
   k_max_reduce<<<(int)blocks, 256, 0, s>>>(a, n, out);
+}
+
+void launch_build_segments(int32_t N, const int64_t* row_ptr, const uint32_t* col,
+                           const uint8_t* delay, int32_t shift, int32_t dmax, void* seg,
+                           int32_t seg_kind, cudaStream_t s) {
+  int64_t blocks = ((int64_t)N * 32 + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  k_build_segments<<<(int)blocks, 256, 0, s>>>(N, row_ptr, col, delay, shift, dmax, seg, seg_kind);
 }
 
 }  // namespace dbn

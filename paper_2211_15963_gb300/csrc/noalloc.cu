@@ -15,7 +15,8 @@
 // The same kernels as dbnet_step run here (init, deliver, update), so results
 // are identical to dbnet_create + dbnet_step on the same graph and options.
 // All calls share the scratch; each call clears it first; overlapping calls
-// race.
+// race.  Without room for a per-graph segment table, the delivery finds each
+// spike's due segment by binary search over its row's delays.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,24 +43,22 @@ constexpr int kMaxTiles = kMaxN / kTile;
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets inside the scratch array.
-constexpr size_t kOffList0 = 0;
-constexpr size_t kOffList1 = align256(kOffList0 + sizeof(Entry) * kMaxLive);
-constexpr size_t kOffAcc = align256(kOffList1 + sizeof(Entry) * kMaxLive);
+constexpr size_t kOffHist = 0;  // spike ring: kMaxLive entries
+constexpr size_t kOffAcc = align256(kOffHist + sizeof(uint32_t) * kMaxLive);
 constexpr size_t kOffIndeg = align256(kOffAcc + sizeof(int2) * kMaxN);
 constexpr size_t kOffRc = align256(kOffIndeg + sizeof(int32_t) * kMaxN);
 constexpr size_t kOffRo = align256(kOffRc + sizeof(RegionConst) * kMaxR);
 constexpr size_t kOffDesc = align256(kOffRo + sizeof(int32_t) * (kMaxR + 1));
 constexpr size_t kOffDyn = align256(kOffDesc + sizeof(InstDesc));
 constexpr size_t kOffTiles = align256(kOffDyn + sizeof(InstDyn));
-constexpr size_t kOffRegInst = align256(kOffTiles + sizeof(int32_t) * kMaxTiles);
+constexpr size_t kOffRegInst = align256(kOffTiles + sizeof(int4) * kMaxTiles);
 constexpr size_t kOffCnt = align256(kOffRegInst + sizeof(int32_t) * kMaxR);
 constexpr size_t kOffBw = align256(kOffCnt + sizeof(int32_t) * kMaxR);
 constexpr size_t kOffYlast = align256(kOffBw + sizeof(double) * 4 * kMaxR);
-constexpr size_t kOffCount = align256(kOffYlast + sizeof(double) * kMaxR);   // uint32[2]
-constexpr size_t kOffIter = align256(kOffCount + sizeof(uint32_t) * 2);      // u64
-constexpr size_t kOffEvents = align256(kOffIter + sizeof(unsigned long long));
-constexpr size_t kOffDone = align256(kOffEvents + sizeof(unsigned long long));
-constexpr size_t kOffFlags = align256(kOffDone + sizeof(unsigned));
+constexpr size_t kOffHcount = align256(kOffYlast + sizeof(double) * kMaxR);  // uint32[256]
+constexpr size_t kOffClosed = align256(kOffHcount + sizeof(uint32_t) * 256);  // int64[kMaxR]
+constexpr size_t kOffEvents = align256(kOffClosed + sizeof(long long) * kMaxR);
+constexpr size_t kOffFlags = align256(kOffEvents + sizeof(unsigned long long));
 constexpr size_t kOffScal = align256(kOffFlags + sizeof(unsigned));          // uint32[4]
 constexpr size_t kScratchUsed = align256(kOffScal + sizeof(unsigned) * 4);
 // everything from kOffAcc on is cleared at the start of every call
@@ -213,17 +212,16 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     for (int32_t r = 0; r < R; ++r) wext_max = std::max(wext_max, params[r].w_ext);
     const int S = choose_shift(gd, wext_max, options->fixed_shift);
 
-    // region constants and the live-list bound
+    // region constants and the spike-ring bound (a slot per step of the
+    // longest delay, each able to hold every neuron)
     RegionConst rc[kMaxR];
-    int min_nref = 255;
-    for (int32_t r = 0; r < R; ++r) {
+    for (int32_t r = 0; r < R; ++r)
       rc[r] = region_const(params[r], options->dt_ms, S, ro[r], ro[r + 1], ro[r] + graph->n_exc[r]);
-      min_nref = std::min(min_nref, (int)rc[r].n_ref);
-    }
-    const uint64_t live = (uint64_t)N * (uint64_t)((dmax + min_nref) / (min_nref + 1));
-    if (live > kMaxLive)
-      raise(DBNET_ERANGE, "spikes in flight could reach " + std::to_string(live) +
-                              " entries, above the allocation-free limit " + std::to_string(kMaxLive));
+    const uint64_t ring = (uint64_t)n_pad * (uint64_t)(dmax + 1);
+    if (ring > kMaxLive)
+      raise(DBNET_ERANGE, "a spike ring of " + std::to_string(ring) +
+                              " entries (padded neurons x (longest delay + 1)) is above the "
+                              "allocation-free limit " + std::to_string(kMaxLive));
 
     InstDesc d;
     std::memset(&d, 0, sizeof(d));
@@ -231,6 +229,9 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     d.col = reinterpret_cast<const uint32_t*>(graph->col);
     d.w = graph->weight_bf16;
     d.delay = graph->delay;  // separate delay array: targets are used as given
+    d.seg = nullptr;         // segments found by binary search over each row's delays
+    d.seg_kind = kSegSearch;
+    d.dmax = dmax;
     d.region_offsets = reinterpret_cast<const int32_t*>(at(kOffRo));
     d.rc = reinterpret_cast<const RegionConst*>(at(kOffRc));
     d.bold = nullptr;
@@ -266,7 +267,17 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
       bw[4 * r] = 0.0;
       bw[4 * r + 1] = bw[4 * r + 2] = bw[4 * r + 3] = 1.0;
     }
-    // tile and region owner tables stay zero (one instance) after the clear
+    // per tile: instance 0, first region, regions touched; region owners stay 0
+    int4 tiles[kMaxTiles];
+    for (int t = 0; t < n_tiles; ++t) {
+      const int32_t lo = t * kTile, hi = std::min((t + 1) * kTile, N) - 1;
+      int32_t r0 = 0, r1 = 0;
+      while (ro[r0 + 1] <= lo) ++r0;
+      r1 = r0;
+      while (ro[r1 + 1] <= hi) ++r1;
+      tiles[t] = make_int4(0, r0, r1 - r0 + 1, 0);
+    }
+    CK(cudaMemcpyAsync(at(kOffTiles), tiles, sizeof(int4) * n_tiles, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(at(kOffRc), rc, sizeof(RegionConst) * R, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(at(kOffRo), ro, sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(at(kOffDesc), &d, sizeof(d), cudaMemcpyHostToDevice, s));
@@ -281,19 +292,18 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     e.stride = n_pad;
     e.insts = reinterpret_cast<const InstDesc*>(at(kOffDesc));
     e.dyn = reinterpret_cast<InstDyn*>(at(kOffDyn));
-    e.tile_inst = reinterpret_cast<const int32_t*>(at(kOffTiles));
+    e.tile_info = reinterpret_cast<const int4*>(at(kOffTiles));
+    e.closed = reinterpret_cast<long long*>(at(kOffClosed));
     e.cnt = reinterpret_cast<int32_t*>(at(kOffCnt));
     e.bw = reinterpret_cast<double*>(at(kOffBw));
     e.ylast = reinterpret_cast<double*>(at(kOffYlast));
     e.region_inst = reinterpret_cast<const int32_t*>(at(kOffRegInst));
-    e.list0 = reinterpret_cast<Entry*>(at(kOffList0));
-    e.list1 = reinterpret_cast<Entry*>(at(kOffList1));
-    e.count = reinterpret_cast<uint32_t*>(at(kOffCount));
-    e.iter = reinterpret_cast<unsigned long long*>(at(kOffIter));
-    e.done = reinterpret_cast<unsigned*>(at(kOffDone));
+    e.hist = reinterpret_cast<uint32_t*>(at(kOffHist));
+    e.hcount = reinterpret_cast<uint32_t*>(at(kOffHcount));
+    e.hist_cap = n_pad;
+    e.D = dmax + 1;
     e.events = reinterpret_cast<unsigned long long*>(at(kOffEvents));
     e.flags = reinterpret_cast<unsigned*>(at(kOffFlags));
-    e.list_cap = kMaxLive;
     e.n_inst = 1;
     e.n_tiles = n_tiles;
     e.total_R = R;
@@ -301,9 +311,11 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     launch_init_state(e, 0, n_tiles, 0, s);
     const int grid = deliver_grid();
     for (int64_t k = 0; k < n_steps; ++k) {
-      launch_deliver(e, grid, s);
-      launch_update(e, s);
+      const StepRef sr{nullptr, (unsigned long long)k, nullptr};
+      launch_deliver(e, grid, sr, s);
+      launch_update(e, sr, s);
     }
+    launch_close(e, (unsigned long long)n_steps, s);
     CK(cudaGetLastError());
     InstDyn out_dyn;
     unsigned long long ev = 0;
@@ -312,7 +324,7 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     CK(cudaMemcpyAsync(&ev, at(kOffEvents), sizeof(ev), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&flags, at(kOffFlags), sizeof(flags), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (flags & kFlagListOverflow) raise(DBNET_ERANGE, "live delivery list overflowed");
+    if (flags & kFlagHistOverflow) raise(DBNET_ERANGE, "spike ring overflowed");
     *n_spikes = (int64_t)out_dyn.spikes;
     *n_events = (int64_t)ev;
     return DBNET_OK;
