@@ -35,7 +35,6 @@ constexpr int kUpdThreads = 256;    // four neurons per thread
 constexpr int kDelThreads = 256;
 constexpr int kMaxThr = 16;         // Poisson inversion thresholds
 constexpr int kTileRegions = 8;     // region constants staged in shared memory
-constexpr int kLongSeg = 48;        // segments longer than this are shared by a warp
 
 struct RegionConst {
   float dtC, gL, VL, Vth, Vreset, Iext;

@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
   const unsigned long long wstride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned long long wbase = (unsigned long long)blockIdx.x * blockDim.x + warp * 32;
   for (unsigned long long b0 = wbase; b0 < W; b0 += wstride) {  // warp-uniform
+    // each lane resolves one item: (spike, delay) -> its edge segment
     const unsigned long long t = b0 + lane;
-    bool longseg = false;
     int64_t e0 = 0;
     uint32_t nseg = 0;
     int inst = 0;
@@ -404,55 +404,41 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
         }
         nseg = (uint32_t)(b - a);
         e0 = r0 + a;
-        longseg = nseg > (uint32_t)kLongSeg;
-        if (!longseg && nseg > 0) {
-          const uint32_t* __restrict__ col = dd.col;
-          const uint16_t* __restrict__ w = dd.w;
-          const uint32_t tmask = dd.tmask;
-          const float two_S = dd.two_S;
-          int* accp = reinterpret_cast<int*>(e.acc + dd.base) + cls;
-          for (uint32_t o = 0; o < nseg; o += 8) {
-            uint32_t cc[8];
-            uint16_t ww[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              cc[u] = 0u;
-              ww[u] = 0;
-              if (o + u < nseg) {
-                cc[u] = __ldg(col + e0 + o + u);
-                ww[u] = __ldg(w + e0 + o + u);
-              }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              if (o + u < nseg) {
-                const float wf = __uint_as_float((uint32_t)ww[u] << 16);
-                atomicAdd(accp + 2 * (size_t)(cc[u] & tmask), __float2int_rn(__fmul_rn(wf, two_S)));
-              }
-            }
-          }
-          ev += nseg;
-        }
       }
     }
-    // long segments of this warp, one at a time, all lanes (coalesced)
-    unsigned lm = __ballot_sync(kFull, longseg);
-    while (lm) {
-      const int src = __ffs(lm) - 1;
-      lm &= lm - 1;
-      const int64_t q0 = __shfl_sync(kFull, e0, src);
-      const uint32_t qn = __shfl_sync(kFull, nseg, src);
-      const int qi = __shfl_sync(kFull, inst, src);
-      const uint32_t qc = __shfl_sync(kFull, cls, src);
-      const InstDesc& dd = e.insts[qi];
-      int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
-      for (uint32_t o = lane; o < qn; o += 32) {
-        const uint32_t cc = __ldg(dd.col + q0 + o);
-        const float wf = __uint_as_float((uint32_t)__ldg(dd.w + q0 + o) << 16);
+    // the warp's segments laid end to end; consecutive lanes take
+    // consecutive edges (coalesced), the owning item found by a shuffle search
+    uint32_t incl = nseg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += x;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t ex = incl - nseg;
+    for (uint32_t f = 0; f < total; f += 32) {  // warp-uniform
+      const uint32_t fi = f + lane;
+      int L = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int cand = L + step < 32 ? L + step : 31;
+        const uint32_t v = __shfl_sync(kFull, ex, cand);
+        if (L + step < 32 && v <= fi) L = cand;
+      }
+      const int64_t q0 = __shfl_sync(kFull, e0, L);
+      const uint32_t qx = __shfl_sync(kFull, ex, L);
+      const int qi = __shfl_sync(kFull, inst, L);
+      const uint32_t qc = __shfl_sync(kFull, cls, L);
+      if (fi < total) {
+        const InstDesc& dd = e.insts[qi];
+        const int64_t ei = q0 + (int64_t)(fi - qx);
+        const uint32_t cc = __ldg(dd.col + ei);
+        const float wf = __uint_as_float((uint32_t)__ldg(dd.w + ei) << 16);
+        int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
         atomicAdd(accp + 2 * (size_t)(cc & dd.tmask), __float2int_rn(__fmul_rn(wf, dd.two_S)));
       }
-      if (lane == 0) ev += qn;
     }
+    if (lane == 0) ev += total;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
