@@ -111,10 +111,13 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   int64_t max_out = 0;
   for (int32_t j = 0; j < N; ++j) max_out = std::max(max_out, g->row_ptr[j + 1] - g->row_ptr[j]);
   gd->seg_kind = max_out < 65536 ? kSeg16 : kSeg32;
-  const int64_t seg_bytes = (int64_t)N * gd->max_delay * (gd->seg_kind == kSeg16 ? 2 : 4);
+  const int32_t per16 = gd->seg_kind == kSeg16 ? 8 : 4;  // entries per 16 bytes
+  gd->seg_stride = (gd->max_delay + per16 - 1) / per16 * per16;
+  const int64_t seg_bytes = (int64_t)N * gd->seg_stride * (gd->seg_kind == kSeg16 ? 2 : 4);
   gd->seg.alloc(seg_bytes);
+  CK(cudaMemsetAsync(gd->seg.p, 0, (size_t)seg_bytes, s));  // row padding stays zero
   launch_build_segments(N, gd->row_ptr.p, gd->col.p, gd->packed ? nullptr : gd->delay.p,
-                        gd->shift, gd->max_delay, gd->seg.p, gd->seg_kind, s);
+                        gd->shift, gd->max_delay, gd->seg_stride, gd->seg.p, gd->seg_kind, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   if (gd->packed) gd->delay.reset();
@@ -293,6 +296,7 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     d.seg = g.seg.p;
     d.seg_kind = g.seg_kind;
     d.dmax = g.max_delay;
+    d.seg_stride = g.seg_stride;
     d.region_offsets = g.ro.p;
     d.rc = ih.rc.p;
     d.bold = ih.bold.p;
@@ -335,6 +339,25 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   if (stride >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "too many neurons in one engine");
   hist.alloc((int64_t)D * stride);
   hcount.alloc(D);
+  // delay-major segment ring: room for seg_cap spikes per step, within about
+  // 2 GiB and an eighth of the free memory; every instance with a u16 table
+  // uses it
+  bool any16 = false;
+  for (int k = 0; k < n; ++k) any16 = any16 || inst[k].graph->seg_kind == kSeg16;
+  int64_t seg_cap = 0;
+  const int32_t dcap = dmax_all;
+  if (any16) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t budget = std::min<int64_t>(int64_t(2) << 30, (int64_t)(free_b / 8));
+    const int64_t per_spike = (int64_t)D * dcap * 2 + (int64_t)D * 8;
+    seg_cap = std::min<int64_t>(stride, budget / per_spike) / 32 * 32;
+    if (seg_cap < 1024) seg_cap = 0;  // too little room to be worth it
+  }
+  if (seg_cap > 0) {
+    hseg.alloc((int64_t)D * dcap * seg_cap);
+    hr0.alloc((int64_t)D * seg_cap);
+  }
   base.alloc(2);
   events.alloc(1);
   flags.alloc(1);
@@ -378,6 +401,10 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   dev.hist = hist.p;
   dev.hcount = hcount.p;
   dev.hist_cap = stride;
+  dev.hseg = hseg.p;
+  dev.hr0 = hr0.p;
+  dev.seg_cap = seg_cap;
+  dev.dcap = dcap;
   dev.D = D;
   dev.events = events.p;
   dev.flags = flags.p;

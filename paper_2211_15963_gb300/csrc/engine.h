@@ -13,8 +13,9 @@
 // Edges of an instance (CSR by source, rows sorted by delay):
 //   col[e] u32 = target | delay << shift  (or target, with delay[e] u8)
 //   w[e]   u16 BF16 bit pattern
-//   seg[j][k] u16/u32 = number of edges of row j with delay <= k + 1,
-//                       k < dmax (the per-delay segment table)
+//   seg[j * seg_stride + k] u16/u32 = number of edges of row j with
+//                       delay <= k + 1, k < dmax (the per-delay segment
+//                       table; seg_stride pads rows to 16 bytes)
 // Iteration g of an engine runs k_deliver then k_update; the bin that ends
 // with iteration g - 1 is closed (Balloon-Windkessel step, BOLD sample) at
 // the start of k_deliver(g), one region per thread.
@@ -22,6 +23,12 @@
 //   global index | class << 31, with a count per slot.  At step n the
 //   delivery reads slots n - d (d = 1..D-1) and applies, for each listed
 //   spike, the segment of its row whose delay is exactly d.
+// Delay-major segment ring (u16 tables only): k_deliver(n) copies, for the
+//   first seg_cap spikes of step n - 1, the row start into hr0[slot][k] and
+//   the row's segment counts into hseg[slot][d][k] (d < dcap), so that the
+//   items (spike k, delay d) of later steps resolve with coalesced loads.
+//   Spikes beyond seg_cap, delay-1 items and u32 tables read the graph's
+//   own row_ptr and segment table instead.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,7 +77,7 @@ struct InstDesc {
   uint32_t tmask;
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;
-  int32_t seg_kind, dmax;
+  int32_t seg_kind, dmax, seg_stride, pad_s;
   double h_bw, z_scale, kappa, gamma, tau, alpha, rho, V0;
 };
 
@@ -113,6 +120,10 @@ struct EngineDev {
   uint32_t* hist;        // [D][hist_cap]
   uint32_t* hcount;      // [D]
   int64_t hist_cap;
+  uint16_t* hseg;        // [D][dcap][seg_cap]
+  int64_t* hr0;          // [D][seg_cap]
+  int64_t seg_cap;       // 0: no segment ring
+  int32_t dcap, pad_h;
   unsigned long long* events;
   unsigned int* flags;
   int32_t D;
@@ -134,8 +145,8 @@ void launch_validate_pack(int32_t N, const int64_t* row_ptr, uint32_t* col, cons
                           unsigned* dmax, unsigned* err, cudaStream_t s);
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s);
 void launch_build_segments(int32_t N, const int64_t* row_ptr, const uint32_t* col,
-                           const uint8_t* delay, int32_t shift, int32_t dmax, void* seg,
-                           int32_t seg_kind, cudaStream_t s);
+                           const uint8_t* delay, int32_t shift, int32_t dmax,
+                           int32_t seg_stride, void* seg, int32_t seg_kind, cudaStream_t s);
 
 enum : unsigned {
   kErrTarget = 1u,

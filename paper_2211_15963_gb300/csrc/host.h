@@ -73,8 +73,8 @@ struct GraphDev {
   DevBuf<uint16_t> w;
   DevBuf<uint8_t> delay;
   DevBuf<int32_t> ro;
-  DevBuf<uint8_t> seg;  // [N][max_delay] u16 or u32 segment table
-  int32_t seg_kind = 0;
+  DevBuf<uint8_t> seg;  // [N][seg_stride] u16 or u32 segment table
+  int32_t seg_kind = 0, seg_stride = 0;
   int32_t shift = 32;
   uint32_t tmask = 0xFFFFFFFFu;
   bool packed = false;
@@ -117,6 +117,8 @@ struct Engine {
   DevBuf<long long> closed;
   DevBuf<double> bw, ylast;
   DevBuf<uint32_t> hist, hcount;
+  DevBuf<uint16_t> hseg;
+  DevBuf<int64_t> hr0;
   DevBuf<unsigned long long> base, events;  // base: the two graph-half iteration words
   DevBuf<unsigned> flags;
   unsigned long long g_host = 0;            // iterations enqueued so far

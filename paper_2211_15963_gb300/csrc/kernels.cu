@@ -329,6 +329,53 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
   for (int gr = gtid; gr < e.total_R; gr += gridDim.x * blockDim.x) close_region(e, gr, g);
   // the slot this iteration's update will fill was last read by the previous one
   if (gtid == 0) e.hcount[g % (unsigned long long)D] = 0u;
+  // The leading nA blocks copy the row start and segment counts of the
+  // previous step's spikes into the delay-major ring (thread per spike, so
+  // each store of a delay plane is coalesced across the warp) and take no
+  // items; nA follows that step's spike count, the same in every block.
+  unsigned long long c1 = 0;
+  int nA = 0;
+  const unsigned long long s1 = (g + (unsigned long long)D - 1ull) % (unsigned long long)D;
+  if (e.seg_cap > 0 && g >= 1ull) {
+    c1 = e.hcount[s1];
+    if (c1 > (unsigned long long)e.hist_cap) c1 = (unsigned long long)e.hist_cap;
+    if (c1 > (unsigned long long)e.seg_cap) c1 = (unsigned long long)e.seg_cap;
+    const unsigned long long want = (c1 + kDelThreads - 1) / kDelThreads;
+    const int most = gridDim.x >= 16 ? (int)gridDim.x / 8 : 1;  // the host launches >= 2 blocks
+    nA = want < (unsigned long long)most ? (int)want : most;
+  }
+  if ((int)blockIdx.x < nA) {
+    const size_t cap = (size_t)e.seg_cap;
+    for (unsigned long long k = gtid; k < c1; k += (unsigned long long)nA * kDelThreads) {
+      const uint32_t ent = e.hist[s1 * (unsigned long long)e.hist_cap + k];
+      const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
+      const int inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
+      const InstDesc& dd = e.insts[inst];
+      if (dd.seg_kind != kSeg16) continue;
+      const int64_t j = gidx - dd.base;
+      e.hr0[s1 * cap + k] = __ldg(dd.row_ptr + j);
+      const uint4* T = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(dd.seg) +
+                                                      j * dd.seg_stride);
+      uint16_t* H = e.hseg + (s1 * (size_t)e.dcap) * cap + k;
+      const int nq = (dd.dmax + 7) >> 3;
+      for (int q0 = 0; q0 < nq; q0 += 4) {
+        uint4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = q0 + i < nq ? __ldg(T + q0 + i) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t wd[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int dl = (q0 + i) * 8 + u;
+            if (dl < dd.dmax) H[(size_t)dl * cap] = (uint16_t)(wd[u >> 1] >> ((u & 1) * 16));
+          }
+        }
+      }
+    }
+    return;
+  }
+  const int bB = (int)blockIdx.x - nA, nB = (int)gridDim.x - nA;  // item blocks
 
   // spikes of step g - d for d = threadIdx.x + 1, and their exclusive prefix
   unsigned long long c = 0;
@@ -361,8 +408,8 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
   __syncthreads();
 
   unsigned long long ev = 0;
-  const unsigned long long wstride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long wbase = (unsigned long long)blockIdx.x * blockDim.x + warp * 32;
+  const unsigned long long wstride = (unsigned long long)nB * blockDim.x;
+  const unsigned long long wbase = (unsigned long long)bB * blockDim.x + warp * 32;
   for (unsigned long long b0 = wbase; b0 < W; b0 += wstride) {  // warp-uniform
     // each lane resolves one item: (spike, delay) -> its edge segment
     const unsigned long long t = b0 + lane;
@@ -387,17 +434,26 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
       const InstDesc& dd = e.insts[inst];
       if ((int32_t)d <= dd.dmax) {
         const int64_t j = gidx - dd.base;
-        const int64_t r0 = __ldg(dd.row_ptr + j);
-        int64_t a, b;
-        if (dd.seg_kind == kSeg16) {
-          const uint16_t* T = static_cast<const uint16_t*>(dd.seg) + j * dd.dmax;
+        int64_t r0, a, b;
+        if (dd.seg_kind == kSeg16 && d >= 2u && k < (unsigned long long)e.seg_cap) {
+          // from the delay-major ring (consecutive lanes, consecutive spikes)
+          const size_t cap = (size_t)e.seg_cap;
+          r0 = __ldg(e.hr0 + slot * cap + k);
+          const uint16_t* H = e.hseg + (slot * (size_t)e.dcap) * cap + k;
+          a = (int64_t)__ldg(H + (size_t)(d - 2u) * cap);
+          b = (int64_t)__ldg(H + (size_t)(d - 1u) * cap);
+        } else if (dd.seg_kind == kSeg16) {
+          r0 = __ldg(dd.row_ptr + j);
+          const uint16_t* T = static_cast<const uint16_t*>(dd.seg) + j * dd.seg_stride;
           a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
           b = (int64_t)__ldg(T + d - 1);
         } else if (dd.seg_kind == kSeg32) {
-          const uint32_t* T = static_cast<const uint32_t*>(dd.seg) + j * dd.dmax;
+          r0 = __ldg(dd.row_ptr + j);
+          const uint32_t* T = static_cast<const uint32_t*>(dd.seg) + j * dd.seg_stride;
           a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
           b = (int64_t)__ldg(T + d - 1);
         } else {
+          r0 = __ldg(dd.row_ptr + j);
           const int64_t r1 = __ldg(dd.row_ptr + j + 1);
           a = first_delay_at_least(dd.col, dd.delay, dd.shift, r0, r1, d) - r0;
           b = first_delay_at_least(dd.col, dd.delay, dd.shift, r0 + a, r1, d + 1) - r0;
@@ -456,14 +512,15 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
 // Warp per row; every entry is written once.
 __global__ void k_build_segments(int32_t N, const int64_t* __restrict__ row_ptr,
                                  const uint32_t* __restrict__ col, const uint8_t* __restrict__ dl,
-                                 int32_t shift, int32_t dmax, void* seg, int32_t kind) {
+                                 int32_t shift, int32_t dmax, int32_t stride, void* seg,
+                                 int32_t kind) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = warp; j < N; j += nwarps) {
     const int64_t a = row_ptr[j], n = row_ptr[j + 1] - a;
-    uint16_t* T16 = static_cast<uint16_t*>(seg) + j * dmax;
-    uint32_t* T32 = static_cast<uint32_t*>(seg) + j * dmax;
+    uint16_t* T16 = static_cast<uint16_t*>(seg) + j * stride;
+    uint32_t* T32 = static_cast<uint32_t*>(seg) + j * stride;
     auto put = [&](int k, uint32_t v) {
       if (kind == kSeg16) T16[k] = (uint16_t)v; else T32[k] = v;
     };
@@ -582,6 +639,7 @@ int deliver_grid() {
 }
 
 void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s) {
+  if (grid < 2) grid = 2;  // with a segment ring, block 0 may take no items
   k_deliver<<<grid, kDelThreads, 0, s>>>(e, sr);
 }
 
@@ -604,12 +662,13 @@ void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t 
 }
 
 void launch_build_segments(int32_t N, const int64_t* row_ptr, const uint32_t* col,
-                           const uint8_t* delay, int32_t shift, int32_t dmax, void* seg,
-                           int32_t seg_kind, cudaStream_t s) {
+                           const uint8_t* delay, int32_t shift, int32_t dmax,
+                           int32_t seg_stride, void* seg, int32_t seg_kind, cudaStream_t s) {
   int64_t blocks = ((int64_t)N * 32 + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  k_build_segments<<<(int)blocks, 256, 0, s>>>(N, row_ptr, col, delay, shift, dmax, seg, seg_kind);
+  k_build_segments<<<(int)blocks, 256, 0, s>>>(N, row_ptr, col, delay, shift, dmax, seg_stride,
+                                                seg, seg_kind);
 }
 
 }  // namespace dbn
