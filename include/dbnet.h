@@ -130,7 +130,7 @@ typedef struct {
   int64_t bold_samples;      /* BOLD samples recorded */
   int32_t fixed_shift;       /* S in use */
   int32_t max_delay;         /* longest delay of the graph, steps */
-  int32_t packed_edges;      /* 1 when target and delay share one 32-bit word */
+  int32_t packed_edges;      /* 1: edges held as 6-byte (target, BF16 weight) records */
   int32_t weights_rounded;   /* 1 when some float32 weight was not a BF16 value */
 } dbnet_stats_t;
 

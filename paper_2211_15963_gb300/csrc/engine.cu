@@ -1,10 +1,11 @@
 // Host engine and the dbnet_* C ABI (see include/dbnet.h).
 //
 // Create: host-side checks that cost O(N + R), then the edge arrays are
-// copied to the device, validated and packed by one warp-per-row kernel
-// (target range, delay range and order, weights -> BF16, in-degrees, largest
-// weight and delay), the per-delay segment table of every row is built, the
-// fixed-point scale is chosen from those, the region
+// copied to the device in chunks of rows, each chunk validated by one
+// warp-per-row kernel (target range, delay range and order, weights -> BF16,
+// in-degrees, largest weight) that writes the interleaved edge records and
+// the per-delay segment table of its rows, the fixed-point scale is chosen
+// from those, the region
 // constants are derived in FP64 and rounded to FP32 once, and the initial
 // state is drawn on the device.
 //
@@ -56,41 +57,60 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   gd->E = E;
   gd->ro_h.assign(g->region_offsets, g->region_offsets + R + 1);
   gd->nexc_h.assign(g->n_exc, g->n_exc + R);
-  int bits = 1;
-  while (bits < 31 && ((int64_t)1 << bits) < (int64_t)N) ++bits;
-  gd->packed = bits <= 24;
-  gd->shift = gd->packed ? bits : 32;
-  gd->tmask = gd->packed ? (uint32_t)((1u << bits) - 1u) : 0xFFFFFFFFu;
+  // the largest delay and row length fix the segment table's shape
+  unsigned dmax_h = 0;
+  for (int64_t e = 0; e < E; ++e) dmax_h = std::max<unsigned>(dmax_h, g->delay[e]);
+  gd->max_delay = (int32_t)std::max(1u, dmax_h);
+  int64_t max_out = 0;
+  for (int32_t j = 0; j < N; ++j) max_out = std::max(max_out, g->row_ptr[j + 1] - g->row_ptr[j]);
+  gd->seg_kind = max_out < 65536 ? kSeg16 : kSeg32;  // u16 counts when every row is short
+  const int32_t per16 = gd->seg_kind == kSeg16 ? 8 : 4;  // entries per 16 bytes
+  gd->seg_stride = (gd->max_delay + per16 - 1) / per16 * per16;
+  const int64_t seg_bytes = (int64_t)N * gd->seg_stride * (gd->seg_kind == kSeg16 ? 2 : 4);
 
   gd->row_ptr.alloc(N + 1);
   gd->ro.alloc(R + 1);
-  gd->col.alloc(std::max<int64_t>(E, 1));
-  gd->w.alloc(std::max<int64_t>(E, 1));
-  gd->delay.alloc(std::max<int64_t>(E, 1));
+  gd->rec.alloc(std::max<int64_t>(3 * E, 1));
+  gd->seg.alloc(seg_bytes);
   CK(cudaMemcpyAsync(gd->row_ptr.p, g->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(gd->ro.p, g->region_offsets, sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s));
-  DevBuf<float> wstage;
-  const void* w_in = gd->w.p;
-  if (E > 0) {
-    CK(cudaMemcpyAsync(gd->col.p, g->col, sizeof(int32_t) * E, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(gd->delay.p, g->delay, E, cudaMemcpyHostToDevice, s));
-    if (g->weight_dtype == DBNET_WEIGHT_BF16) {
-      CK(cudaMemcpyAsync(gd->w.p, g->weight, sizeof(uint16_t) * E, cudaMemcpyHostToDevice, s));
-    } else {
-      wstage.alloc(E);
-      CK(cudaMemcpyAsync(wstage.p, g->weight, sizeof(float) * E, cudaMemcpyHostToDevice, s));
-      w_in = wstage.p;
-    }
-  }
+  CK(cudaMemsetAsync(gd->seg.p, 0, (size_t)seg_bytes, s));
   DevBuf<int32_t> indeg;
   indeg.alloc(N);
-  DevBuf<unsigned> scal;  // wmax bits, dmax, err, kin_max
+  DevBuf<unsigned> scal;  // wmax bits, unused, err, kin_max
   scal.alloc(4);
   CK(cudaMemsetAsync(indeg.p, 0, sizeof(int32_t) * N, s));
   CK(cudaMemsetAsync(scal.p, 0, sizeof(unsigned) * 4, s));
-  if (E > 0)
-    launch_validate_pack(N, gd->row_ptr.p, gd->col.p, w_in, g->weight_dtype, gd->w.p,
-                         gd->delay.p, gd->shift, indeg.p, scal.p + 0, scal.p + 1, scal.p + 2, s);
+  // rows in chunks of about kIngestEdges edges through staging buffers, so
+  // the device never holds more than the records and one chunk
+  if (E > 0) {
+    constexpr int64_t kIngestEdges = int64_t(1) << 27;
+    const int64_t cap = std::min(E, std::max(kIngestEdges, max_out));
+    const int64_t wsz = g->weight_dtype == DBNET_WEIGHT_BF16 ? 2 : 4;
+    DevBuf<int32_t> col_st;
+    DevBuf<uint8_t> w_st, d_st;
+    col_st.alloc(cap);
+    w_st.alloc(cap * wsz);
+    d_st.alloc(cap);
+    int32_t j0 = 0;
+    while (j0 < N) {
+      int32_t j1 = j0 + 1;
+      while (j1 < N && g->row_ptr[j1 + 1] - g->row_ptr[j0] <= cap) ++j1;
+      const int64_t e0 = g->row_ptr[j0], ne = g->row_ptr[j1] - e0;
+      if (ne > 0) {
+        CK(cudaMemcpyAsync(col_st.p, g->col + e0, sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_st.p, g->delay + e0, ne, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(w_st.p, static_cast<const uint8_t*>(g->weight) + e0 * wsz, ne * wsz,
+                           cudaMemcpyHostToDevice, s));
+        launch_ingest(N, j0, j1, e0, gd->row_ptr.p, col_st.p, w_st.p, g->weight_dtype, d_st.p,
+                      gd->rec.p, gd->max_delay, gd->seg_stride, gd->seg.p, gd->seg_kind, indeg.p,
+                      scal.p + 0, scal.p + 2, s);
+        CK(cudaGetLastError());
+      }
+      j0 = j1;
+    }
+    CK(cudaStreamSynchronize(s));  // the staging buffers are freed next
+  }
   launch_max_reduce(indeg.p, N, scal.p + 3, s);
   CK(cudaGetLastError());
   unsigned h[4];
@@ -105,22 +125,7 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   float wmax;
   std::memcpy(&wmax, &h[0], 4);
   gd->w_max = (double)wmax;
-  gd->max_delay = (int32_t)std::max(1u, h[1]);
   gd->kin_max = (int32_t)h[3];
-  // segment table: u16 counts when every row has fewer than 2^16 edges
-  int64_t max_out = 0;
-  for (int32_t j = 0; j < N; ++j) max_out = std::max(max_out, g->row_ptr[j + 1] - g->row_ptr[j]);
-  gd->seg_kind = max_out < 65536 ? kSeg16 : kSeg32;
-  const int32_t per16 = gd->seg_kind == kSeg16 ? 8 : 4;  // entries per 16 bytes
-  gd->seg_stride = (gd->max_delay + per16 - 1) / per16 * per16;
-  const int64_t seg_bytes = (int64_t)N * gd->seg_stride * (gd->seg_kind == kSeg16 ? 2 : 4);
-  gd->seg.alloc(seg_bytes);
-  CK(cudaMemsetAsync(gd->seg.p, 0, (size_t)seg_bytes, s));  // row padding stays zero
-  launch_build_segments(N, gd->row_ptr.p, gd->col.p, gd->packed ? nullptr : gd->delay.p,
-                        gd->shift, gd->max_delay, gd->seg_stride, gd->seg.p, gd->seg_kind, s);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(s));
-  if (gd->packed) gd->delay.reset();
   return gd;
 }
 
@@ -290,9 +295,10 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     InstDesc& d = desc_h[(size_t)k];
     std::memset(&d, 0, sizeof(d));
     d.row_ptr = g.row_ptr.p;
-    d.col = g.col.p;
-    d.w = g.w.p;
-    d.delay = g.packed ? nullptr : g.delay.p;
+    d.rec = g.rec.p;
+    d.col = nullptr;
+    d.w = nullptr;
+    d.delay = nullptr;
     d.seg = g.seg.p;
     d.seg_kind = g.seg_kind;
     d.dmax = g.max_delay;
@@ -310,8 +316,8 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     d.N = g.N;
     d.R = g.R;
     d.rbase = ih.rbase;
-    d.shift = g.shift;
-    d.tmask = g.tmask;
+    d.shift = 32;
+    d.tmask = 0xFFFFFFFFu;
     d.two_S = std::ldexp(1.0f, S);
     d.inv_two_S = std::ldexp(1.0f, -S);
     d.spb = (int32_t)std::lrint(o.bin_ms / o.dt_ms);

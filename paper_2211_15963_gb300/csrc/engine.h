@@ -10,9 +10,11 @@
 // HBM layout (per global neuron i, stride = padded neuron count):
 //   V[i] f32 | J[u * stride + i] f32, u = AMPA, NMDA, GABA_A, GABA_B |
 //   ref[i] u8 (remaining refractory steps) | acc[i] int2 (E, I fixed point)
-// Edges of an instance (CSR by source, rows sorted by delay):
-//   col[e] u32 = target | delay << shift  (or target, with delay[e] u8)
-//   w[e]   u16 BF16 bit pattern
+// Edges of an instance (CSR by source, rows sorted by delay), either
+//   rec[3e], rec[3e+1], rec[3e+2] u16 = target low, target high, BF16 weight
+//     (interleaved 6-byte records: a short segment is one contiguous read), or,
+//   for graphs the caller keeps (the allocation-free entry point), arrays
+//   col[e] u32 = target, w[e] u16 BF16 bit pattern, delay[e] u8
 //   seg[j * seg_stride + k] u16/u32 = number of edges of row j with
 //                       delay <= k + 1, k < dmax (the per-delay segment
 //                       table; seg_stride pads rows to 16 bytes)
@@ -59,6 +61,7 @@ enum : int32_t {
 
 struct InstDesc {
   const int64_t* row_ptr;
+  const uint16_t* rec;           // interleaved records, or nullptr for col/w/delay
   const uint32_t* col;
   const uint16_t* w;
   const uint8_t* delay;          // nullptr when the delay is packed into col
@@ -139,14 +142,12 @@ void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s);
 void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s);
 void launch_set_base(unsigned long long* base, unsigned long long g, cudaStream_t s);
 int deliver_grid();
-void launch_validate_pack(int32_t N, const int64_t* row_ptr, uint32_t* col, const void* w_in,
-                          int32_t w_dtype, uint16_t* w_out, const uint8_t* delay_in,
-                          int32_t shift, int32_t* indeg, unsigned* wmax_bits,
-                          unsigned* dmax, unsigned* err, cudaStream_t s);
+void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,
+                   const int32_t* col_in, const void* w_in, int32_t w_dtype,
+                   const uint8_t* delay_in, uint16_t* rec, int32_t dmax, int32_t seg_stride,
+                   void* seg, int32_t seg_kind, int32_t* indeg, unsigned* wmax_bits, unsigned* err,
+                   cudaStream_t s);
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s);
-void launch_build_segments(int32_t N, const int64_t* row_ptr, const uint32_t* col,
-                           const uint8_t* delay, int32_t shift, int32_t dmax,
-                           int32_t seg_stride, void* seg, int32_t seg_kind, cudaStream_t s);
 
 enum : unsigned {
   kErrTarget = 1u,

@@ -69,15 +69,11 @@ struct GraphDev {
   int64_t E = 0;
   std::vector<int32_t> ro_h, nexc_h;
   DevBuf<int64_t> row_ptr;
-  DevBuf<uint32_t> col;
-  DevBuf<uint16_t> w;
-  DevBuf<uint8_t> delay;
+  DevBuf<uint16_t> rec;  // [3E] interleaved (target lo, target hi, BF16 weight)
   DevBuf<int32_t> ro;
   DevBuf<uint8_t> seg;  // [N][seg_stride] u16 or u32 segment table
   int32_t seg_kind = 0, seg_stride = 0;
-  int32_t shift = 32;
-  uint32_t tmask = 0xFFFFFFFFu;
-  bool packed = false;
+  bool packed = true;  // edges held as interleaved records
   bool rounded = false;
   int32_t max_delay = 1, kin_max = 0;
   double w_max = 0.0;

@@ -488,10 +488,18 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
       if (fi < total) {
         const InstDesc& dd = e.insts[qi];
         const int64_t ei = q0 + (int64_t)(fi - qx);
-        const uint32_t cc = __ldg(dd.col + ei);
-        const float wf = __uint_as_float((uint32_t)__ldg(dd.w + ei) << 16);
+        uint32_t tg, wb;
+        if (dd.rec) {
+          const uint16_t* r3 = dd.rec + 3 * ei;
+          tg = (uint32_t)__ldg(r3) | ((uint32_t)__ldg(r3 + 1) << 16);
+          wb = __ldg(r3 + 2);
+        } else {
+          tg = __ldg(dd.col + ei) & dd.tmask;
+          wb = __ldg(dd.w + ei);
+        }
+        const float wf = __uint_as_float(wb << 16);
         int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
-        atomicAdd(accp + 2 * (size_t)(cc & dd.tmask), __float2int_rn(__fmul_rn(wf, dd.two_S)));
+        atomicAdd(accp + 2 * (size_t)tg, __float2int_rn(__fmul_rn(wf, dd.two_S)));
       }
     }
     if (lane == 0) ev += total;
@@ -508,76 +516,65 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
   }
 }
 
-// Segment table: seg[j][k] = number of edges of row j with delay <= k + 1.
-// Warp per row; every entry is written once.
-__global__ void k_build_segments(int32_t N, const int64_t* __restrict__ row_ptr,
-                                 const uint32_t* __restrict__ col, const uint8_t* __restrict__ dl,
-                                 int32_t shift, int32_t dmax, int32_t stride, void* seg,
-                                 int32_t kind) {
+// Ingest rows [j0, j1) of a graph from staging arrays that hold its edges
+// from e_base on: warp per source row.  Checks every edge (target range,
+// delay >= 1 and non-decreasing within the row, weight finite and
+// non-negative after rounding to BF16), counts in-degrees, and writes
+//   rec[3e .. 3e+2] = target low 16 bits, target high 16 bits, BF16 weight
+//   seg[j * seg_stride + k] = number of edges of row j with delay <= k + 1
+// (the segment table must be zero on entry; entries below the row's first
+// delay stay zero).
+__global__ void k_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base,
+                         const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_in,
+                         const void* __restrict__ w_in, int32_t w_dtype,
+                         const uint8_t* __restrict__ delay_in, uint16_t* __restrict__ rec,
+                         int32_t dmax, int32_t seg_stride, void* seg, int32_t kind,
+                         int32_t* indeg, unsigned* wmax_bits, unsigned* err) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = warp; j < N; j += nwarps) {
-    const int64_t a = row_ptr[j], n = row_ptr[j + 1] - a;
-    uint16_t* T16 = static_cast<uint16_t*>(seg) + j * stride;
-    uint32_t* T32 = static_cast<uint32_t*>(seg) + j * stride;
-    auto put = [&](int k, uint32_t v) {
-      if (kind == kSeg16) T16[k] = (uint16_t)v; else T32[k] = v;
-    };
-    if (n == 0) {
-      for (int k = lane; k < dmax; k += 32) put(k, 0u);
-      continue;
+  unsigned my_err = 0, my_wmax = 0;
+  for (int64_t j = j0 + warp; j < j1; j += nwarps) {
+    const int64_t a = row_ptr[j] - e_base, b = row_ptr[j + 1] - e_base;
+    for (int64_t e = a + lane; e < b; e += 32) {
+      const int32_t t = col_in[e];
+      const unsigned d = delay_in[e];
+      if (t < 0 || t >= N) my_err |= kErrTarget;
+      if (d < 1u) my_err |= kErrDelayRange;
+      if (e > a && delay_in[e - 1] > d) my_err |= kErrDelayOrder;
+      uint16_t wb;
+      if (w_dtype == 1) {
+        wb = static_cast<const uint16_t*>(w_in)[e];
+      } else {
+        const float f = static_cast<const float*>(w_in)[e];
+        const uint32_t u = __float_as_uint(f);
+        const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+        wb = (uint16_t)(r >> 16);
+        if ((uint32_t)wb << 16 != u) my_err |= kErrRounded;
+      }
+      const uint32_t wu = (uint32_t)wb << 16;
+      const float wf = __uint_as_float(wu);
+      if (!(wf >= 0.0f) || isinf(wf)) my_err |= kErrWeight;
+      else my_wmax = max(my_wmax, wu);
+      const uint32_t tu = (uint32_t)t;
+      uint16_t* r3 = rec + 3 * (e_base + e);
+      r3[0] = (uint16_t)(tu & 0xFFFFu);
+      r3[1] = (uint16_t)(tu >> 16);
+      r3[2] = wb;
+      if (t >= 0 && t < N) atomicAdd(indeg + t, 1);
     }
+    // segment counts: edge p closes the delays from its own to the next edge's
+    const int64_t n = b - a;
+    uint16_t* T16 = static_cast<uint16_t*>(seg) + j * seg_stride;
+    uint32_t* T32 = static_cast<uint32_t*>(seg) + j * seg_stride;
     for (int64_t p = lane; p < n; p += 32) {
-      const int dp = (int)edge_delay(col, dl, shift, a + p);
-      const int dn = p + 1 < n ? (int)edge_delay(col, dl, shift, a + p + 1) : dmax + 1;
-      if (p == 0)
-        for (int k = 0; k <= dp - 2; ++k) put(k, 0u);
-      for (int k = dp - 1; k <= dn - 2; ++k) put(k, (uint32_t)(p + 1));
-    }
-  }
-}
-
-// Validate and pack the edges of one graph: warp per source row.
-__global__ void k_validate_pack(int32_t N, const int64_t* __restrict__ row_ptr, uint32_t* col,
-                                const void* __restrict__ w_in, int32_t w_dtype,
-                                uint16_t* __restrict__ w_out, const uint8_t* __restrict__ delay_in,
-                                int32_t shift, int32_t* indeg, unsigned* wmax_bits, unsigned* dmax,
-                                unsigned* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned my_err = 0, my_wmax = 0, my_dmax = 0;
-  for (int64_t j = warp; j < N; j += nwarps) {
-    const int64_t a = row_ptr[j], b = row_ptr[j + 1];
-    for (int64_t e0 = a; e0 < b; e0 += 32) {
-      const int64_t e = e0 + lane;
-      if (e < b) {
-        const int32_t t = (int32_t)col[e];
-        const unsigned d = delay_in[e];
-        if (t < 0 || t >= N) my_err |= kErrTarget;
-        if (d < 1u) my_err |= kErrDelayRange;
-        if (e > a && delay_in[e - 1] > d) my_err |= kErrDelayOrder;
-        uint16_t wb;
-        if (w_dtype == 1) {
-          wb = static_cast<const uint16_t*>(w_in)[e];
-        } else {
-          const float f = static_cast<const float*>(w_in)[e];
-          uint32_t u = __float_as_uint(f);
-          uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);
-          wb = (uint16_t)(r >> 16);
-          if ((uint32_t)wb << 16 != u) my_err |= kErrRounded;
-        }
-        const uint32_t wu = (uint32_t)wb << 16;
-        const float wf = __uint_as_float(wu);
-        if (!(wf >= 0.0f) || isinf(wf)) my_err |= kErrWeight;
-        else my_wmax = max(my_wmax, wu);
-        w_out[e] = wb;
-        my_dmax = max(my_dmax, d);
-        if (t >= 0 && t < N) {
-          atomicAdd(indeg + t, 1);
-          col[e] = shift < 32 ? ((uint32_t)t | ((uint32_t)d << shift)) : (uint32_t)t;
-        }
+      const int dp = (int)delay_in[a + p];
+      const int dn = p + 1 < n ? (int)delay_in[a + p + 1] : dmax + 1;
+      const int k0 = dp - 1 > 0 ? dp - 1 : 0;
+      const int k1 = dn - 2 < dmax - 1 ? dn - 2 : dmax - 1;  // malformed rows fail creation
+      for (int k = k0; k <= k1; ++k) {
+        if (kind == kSeg16) T16[k] = (uint16_t)(p + 1);
+        else T32[k] = (uint32_t)(p + 1);
       }
     }
   }
@@ -585,12 +582,10 @@ __global__ void k_validate_pack(int32_t N, const int64_t* __restrict__ row_ptr, 
   for (int o = 16; o > 0; o >>= 1) {
     my_err |= __shfl_xor_sync(kFull, my_err, o);
     my_wmax = max(my_wmax, __shfl_xor_sync(kFull, my_wmax, o));
-    my_dmax = max(my_dmax, __shfl_xor_sync(kFull, my_dmax, o));
   }
   if (lane == 0) {
     if (my_err) atomicOr(err, my_err);
     atomicMax(wmax_bits, my_wmax);
-    atomicMax(dmax, my_dmax);
   }
 }
 
@@ -643,15 +638,16 @@ void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s) {
   k_deliver<<<grid, kDelThreads, 0, s>>>(e, sr);
 }
 
-void launch_validate_pack(int32_t N, const int64_t* row_ptr, uint32_t* col, const void* w_in,
-                          int32_t w_dtype, uint16_t* w_out, const uint8_t* delay_in,
-                          int32_t shift, int32_t* indeg, unsigned* wmax_bits, unsigned* dmax,
-                          unsigned* err, cudaStream_t s) {
-  int64_t blocks = ((int64_t)N * 32 + 255) / 256;
+void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,
+                   const int32_t* col_in, const void* w_in, int32_t w_dtype,
+                   const uint8_t* delay_in, uint16_t* rec, int32_t dmax, int32_t seg_stride,
+                   void* seg, int32_t seg_kind, int32_t* indeg, unsigned* wmax_bits, unsigned* err,
+                   cudaStream_t s) {
+  int64_t blocks = ((int64_t)(j1 - j0) * 32 + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  k_validate_pack<<<(int)blocks, 256, 0, s>>>(N, row_ptr, col, w_in, w_dtype, w_out, delay_in,
-                                              shift, indeg, wmax_bits, dmax, err);
+  k_ingest<<<(int)blocks, 256, 0, s>>>(N, j0, j1, e_base, row_ptr, col_in, w_in, w_dtype, delay_in,
+                                       rec, dmax, seg_stride, seg, seg_kind, indeg, wmax_bits, err);
 }
 
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s) {
@@ -661,14 +657,5 @@ void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t 
   k_max_reduce<<<(int)blocks, 256, 0, s>>>(a, n, out);
 }
 
-void launch_build_segments(int32_t N, const int64_t* row_ptr, const uint32_t* col,
-                           const uint8_t* delay, int32_t shift, int32_t dmax,
-                           int32_t seg_stride, void* seg, int32_t seg_kind, cudaStream_t s) {
-  int64_t blocks = ((int64_t)N * 32 + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  if (blocks < 1) blocks = 1;
-  k_build_segments<<<(int)blocks, 256, 0, s>>>(N, row_ptr, col, delay, shift, dmax, seg_stride,
-                                                seg, seg_kind);
-}
 
 }  // namespace dbn
