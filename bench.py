@@ -59,6 +59,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--regions", type=int, default=100, help="regions of 20,000 neurons")
     ap.add_argument("--k-in", type=int, default=1000, help="in-degree (80 %% within region)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "ensemble", "serving"],
+                    help="mid: the headline line; ensemble: 64-member HMDA ensemble (steps = "
+                         "TRs) against one network per launch; serving: request stream")
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--separate-trs", type=int, default=1,
+                    help="TRs timed for the one-network-per-launch comparison")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--arrival-hz", type=float, default=4.0)
+    ap.add_argument("--catalogue", type=int, default=16,
+                    help="distinct request networks built before the stream starts")
     return ap.parse_args()
 
 
@@ -337,6 +347,154 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------ ensemble workload ----
+ENS_DRIVE = 3.4007   # I_ext for ~10 Hz in the 100,000-neuron, in-degree-500 network (tune_drive)
+TR_MS = 800.0
+TR_STEPS = 8000
+LOG_LO, LOG_HI = -0.6931471805599453, 0.6931471805599453   # log 0.5, log 2
+
+
+def ensemble_setup(members):
+    """The batched HMDA workload: one shared 100,000-neuron graph (20 regions
+    of 5,000, in-degree 500), per-member per-region AMPA and GABA_A scales
+    drawn log-uniform on [0.5, 2], and a hidden member with its own draw."""
+    import numpy as np
+    import synth
+    g = synth.ensemble_network()
+    base = synth.scale_for_degree(synth.default_region_params(I_ext=ENS_DRIVE), 500)
+    R = g.n_regions
+    theta = np.random.default_rng(synth.seed_for(2) + 2).uniform(LOG_LO, LOG_HI, (members, R, 2))
+    hidden = np.random.default_rng(synth.seed_for(2) + 3).uniform(LOG_LO, LOG_HI, (R, 2))
+    return g, [dict(base) for _ in range(R)], theta, hidden
+
+
+def member_params(base, th):
+    """Region parameters of one member: AMPA and GABA_A conductances scaled by
+    exp(theta) (the same products the ensemble forms on the device)."""
+    import math
+    out = []
+    for r, p in enumerate(base):
+        q = dict(p)
+        gu = list(q["g_u"])
+        gu[0] = gu[0] * math.exp(th[r, 0])
+        gu[2] = gu[2] * math.exp(th[r, 1])
+        q["g_u"] = tuple(gu)
+        out.append(q)
+    return out
+
+
+def run_ensemble(args):
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    from paper_2211_15963_gb300 import dbnet
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    M = args.members
+    g, base, theta, hidden_th = ensemble_setup(M)
+    R = g.n_regions
+    seed = synth.seed_for(2) + 1
+    opts = dict(seed=seed, tr_ms=TR_MS, z_scale=50.0)
+    enkf = dict(obs_var=1e-9, gamma=0.7, rw_sigma=0.01, theta_lo=LOG_LO, theta_hi=LOG_HI)
+    n_tr = args.warmup + args.steps
+
+    # observations: the hidden member's BOLD at every TR (not timed)
+    hidden = dbnet.Network(g, member_params(base, hidden_th), dict(opts, net_id=1 << 20), stream)
+    y_obs = []
+    for _ in range(n_tr):
+        hidden.step(TR_STEPS)
+        y_obs.append(hidden.bold()[-1].copy())
+    hidden.close()
+
+    # batched: every member in each launch, one analysis per TR
+    ens = dbnet.Ensemble(g, base, M, theta, dict(opts, net_id=0), enkf, stream)
+    err0 = float(np.abs(theta[:, :, 0].mean(0) - hidden_th[:, 0]).mean())
+    for k in range(args.warmup):
+        ens.step(TR_STEPS)
+        ens.assimilate(y_obs[k])
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    s0 = ens.stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        ens.step(TR_STEPS)
+        ev[k][1].record(stream)
+        ens.assimilate(y_obs[args.warmup + k])   # reads the predicted mean back (synchronises)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    s1 = ens.stats()
+    sim_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+    an_ms = sum(b.elapsed_time(c) for _, b, c in ev)
+    tot_ms = sim_ms + an_ms
+    events = s1["events"] - s0["events"]
+    spikes = s1["spikes"] - s0["spikes"]
+    th_now, _, _ = ens.read()
+    err1 = float(np.abs(th_now[:, :, 0].mean(0) - hidden_th[:, 0]).mean())
+    ens.close()
+
+    # one network per launch: the same members as independent networks,
+    # stepped one after another, each from its own captured graph
+    sep = []
+    for m in range(M):
+        sep.append(dbnet.Network(g, member_params(base, theta[m]), dict(opts, net_id=m), stream))
+    for net in sep:
+        net.step(TR_STEPS)          # past the onset and the autotuner, like the batched warm-up
+    torch.cuda.synchronize()
+    e0 = sum(n.stats()["events"] for n in sep)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.separate_trs):
+        for net in sep:
+            net.step(TR_STEPS)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sep_ms = a.elapsed_time(b)
+    sep_events = sum(n.stats()["events"] for n in sep) - e0
+    for net in sep:
+        net.close()
+
+    value = events / (tot_ms * 1e-3)
+    sep_value = sep_events / (sep_ms * 1e-3)
+    bio_s = args.steps * TR_MS * 1e-3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators, f64 BOLD and EnKF",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": "HMDA ensemble: %d members x 100,000 neurons (20 regions x 5,000, "
+                               "in-degree 500), TR 800 ms, one FP64 diffusion-EnKF analysis per "
+                               "TR against a hidden member's BOLD" % M,
+                   "members": M, "neurons_per_member": g.n_neurons, "regions": R,
+                   "in_degree": 500, "dt_ms": 0.1, "step": "one TR (8,000 Euler steps + analysis)",
+                   "l2": "not flushed: edges (300 MB) and state (370 MB) exceed L2"},
+        "rtf_ensemble": tot_ms / 1e3 / bio_s,
+        "neuron_updates_per_s": M * g.n_neurons * TR_STEPS * args.steps / (tot_ms * 1e-3),
+        "mean_rate_hz": spikes / (M * g.n_neurons) / bio_s,
+        "analysis_ms_per_tr": an_ms / args.steps, "simulate_ms_per_tr": sim_ms / args.steps,
+        "theta_ampa_mean_abs_err": {"start": err0, "end": err1, "trs": n_tr},
+        "separate": {"value": sep_value, "unit": UNIT, "ms_per_tr": sep_ms / args.separate_trs,
+                     "what": "the same %d members as independent networks, one network's "
+                             "kernels per launch, stepped one after another (simulation only, "
+                             "no analysis)" % M},
+        "batched_over_separate": value / sep_value,
+        "clocks": clk, "gpu_launches": args.steps * (2 * TR_STEPS + 14),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    raise SystemExit("serving workload: not built yet")
+
+
 # -------------------------------------------------------- reference arm ----
 def run_reference(args):
     """The CPU oracle, as it stands, on the host cores: each step is a 10 ms
@@ -383,6 +541,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

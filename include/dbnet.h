@@ -110,7 +110,13 @@ typedef struct {
  *                    arrivals fit int32)
  *   precision        32 (FP32 state; the only mode the device path runs)
  *   raster_capacity  spikes kept for dbnet_read_spikes (0 = none)
- *   bold_capacity    BOLD samples kept per region */
+ *   bold_capacity    BOLD samples kept per region
+ *   autotune_at      step at which the delivery grid is tuned (-1 = never):
+ *                    the next 16 x C steps launch the delivery kernel with
+ *                    each of C candidate grids (1..4 blocks per SM) in turn,
+ *                    timed by CUDA events, and the fastest is kept.  Results
+ *                    do not depend on the grid (integer accumulation).
+ *                    Default 2000 (200 ms at dt 0.1 ms, past the onset). */
 typedef struct {
   double dt_ms, bin_ms, tr_ms, z_scale;
   double bw_kappa, bw_gamma, bw_tau, bw_alpha, bw_rho, bw_V0;
@@ -119,12 +125,15 @@ typedef struct {
   int32_t precision;
   int64_t raster_capacity;
   int64_t bold_capacity;
+  int64_t autotune_at;
 } dbnet_options_t;
 
 typedef struct {
   int64_t step;              /* steps completed */
   int64_t spikes;            /* spikes emitted */
-  int64_t events;            /* synaptic events applied to accumulators */
+  int64_t events;            /* synaptic events applied to accumulators by the
+                                engine behind the handle (for an ensemble member:
+                                the whole ensemble) */
   int64_t raster_len;        /* spikes recorded */
   int64_t raster_dropped;    /* spikes not recorded for lack of capacity */
   int64_t bold_samples;      /* BOLD samples recorded */
@@ -132,6 +141,8 @@ typedef struct {
   int32_t max_delay;         /* longest delay of the graph, steps */
   int32_t packed_edges;      /* 1: edges held as 6-byte (target, BF16 weight) records */
   int32_t weights_rounded;   /* 1 when some float32 weight was not a BF16 value */
+  int32_t deliver_blocks;    /* delivery grid in use */
+  int32_t autotuned;         /* 1 once the autotuner has chosen that grid */
 } dbnet_stats_t;
 
 /* Name of a status code (static string). */
@@ -142,14 +153,15 @@ const char* dbnet_last_error(void);
 
 /* Fill *o with the defaults: dt 0.1 ms, bin 1 ms, TR 800 ms, z_scale 1,
  * the standard hemodynamic constants, seed 1, net_id 0, automatic S,
- * precision 32, no raster, 4096 BOLD samples. */
+ * precision 32, no raster, 4096 BOLD samples, autotune at step 2000. */
 int dbnet_options_default(dbnet_options_t* o);
 
-/* Build a network on the current CUDA device: copy the graph and parameters,
- * validate them on the device, pack the edges (target and delay in one
- * 32-bit word when N <= 2^24, BF16 weight), choose S and set the initial
- * state (V uniform in [V_reset, V_th) from Philox stream 1; traces zero).
- * Also builds the per-row delay-segment table (N x longest delay counts).
+/* Build a network on the current CUDA device: copy the graph and parameters
+ * (edges in chunks of rows through staging buffers), validate them on the
+ * device, store the edges as 6-byte (target, BF16 weight) records, choose S
+ * and set the initial state (V uniform in [V_reset, V_th) from Philox
+ * stream 1; traces zero).  Also builds the per-row delay-segment table
+ * (N x longest delay counts, u16 when every row has < 65536 edges).
  * params: [n_regions].  cuda_stream: a cudaStream_t or NULL.
  * Returns DBNET_EINVAL for a malformed graph or parameter set,
  * DBNET_EOVERFLOW when the chosen S could overflow, DBNET_ENOMEM, DBNET_ECUDA. */

@@ -217,6 +217,7 @@ void check_options(const dbnet_options_t& o) {
     raise(DBNET_EINVAL, "Balloon-Windkessel constants out of range");
   if (!finite(o.z_scale)) raise(DBNET_EINVAL, "z_scale must be finite");
   if (o.fixed_shift < 0 || o.fixed_shift > 30) raise(DBNET_EINVAL, "fixed_shift must be in 0..30");
+  if (o.autotune_at < -1) raise(DBNET_EINVAL, "autotune_at must be -1 or a step index");
 }
 
 // --------------------------------------------------------------- engine ----
@@ -345,9 +346,10 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   if (stride >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "too many neurons in one engine");
   hist.alloc((int64_t)D * stride);
   hcount.alloc(D);
-  // delay-major segment ring: room for seg_cap spikes per step, within about
-  // 2 GiB and an eighth of the free memory; every instance with a u16 table
-  // uses it
+  // delay-major segment ring: room for seg_cap spikes per step -- a 64th of
+  // the neurons (at least 4096), within a sixteenth of the free memory;
+  // every instance with a u16 table uses it, and a step's spikes beyond
+  // seg_cap take the direct path
   bool any16 = false;
   for (int k = 0; k < n; ++k) any16 = any16 || inst[k].graph->seg_kind == kSeg16;
   int64_t seg_cap = 0;
@@ -355,9 +357,10 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   if (any16) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
-    const int64_t budget = std::min<int64_t>(int64_t(2) << 30, (int64_t)(free_b / 8));
+    const int64_t budget = (int64_t)(free_b / 16);
     const int64_t per_spike = (int64_t)D * dcap * 2 + (int64_t)D * 8;
-    seg_cap = std::min<int64_t>(stride, budget / per_spike) / 32 * 32;
+    const int64_t want = std::max<int64_t>(4096, stride / 64);
+    seg_cap = std::min<int64_t>(std::min(stride, want), budget / per_spike) / 32 * 32;
     if (seg_cap < 1024) seg_cap = 0;  // too little room to be worth it
   }
   if (seg_cap > 0) {
@@ -419,6 +422,17 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   dev.total_R = total_R;
   for (int k = 0; k < n; ++k) launch_init_state(dev, k, inst[k].n_tiles, inst[k].first_tile, stream);
   del_grid = deliver_grid();
+  if (specs[0].opt.autotune_at >= 0) {
+    int dev_id = 0, sms = 0;
+    CK(cudaGetDevice(&dev_id));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+    for (int k = 1; k <= 4 && sms * k <= del_grid; ++k) tune_grid.push_back(sms * k);
+    if (tune_grid.size() > 1) {
+      tune_ms.assign(tune_grid.size(), 0.0);
+      tune_pending = true;
+      tune_at = (unsigned long long)specs[0].opt.autotune_at;
+    }
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(stream));
 }
@@ -462,6 +476,67 @@ void Engine::step(int64_t n) {
   check();
   if (n < 0) raise(DBNET_EINVAL, "n_steps must be >= 0");
   if (n == 0) return;
+  while (n > 0) {
+    if (tune_pending && g_host >= tune_at) {
+      n -= tune_steps(n);
+      continue;
+    }
+    const int64_t k = tune_pending ? std::min<int64_t>(n, (int64_t)(tune_at - g_host)) : n;
+    run_plain(k);
+    n -= k;
+  }
+  launch_close(dev, g_host, stream);
+  CK(cudaGetLastError());
+}
+
+// Up to n steps of the autotuner: step i of the tuning run launches its
+// delivery with candidate i mod C between two events.  Returns the steps run.
+int64_t Engine::tune_steps(int64_t n) {
+  const int C = (int)tune_grid.size();
+  const int total = C * kTuneRounds;
+  const int b = (int)std::min<int64_t>(n, total - tune_done);
+  std::vector<cudaEvent_t> ev(2 * (size_t)b, nullptr);
+  for (auto& x : ev) CK(cudaEventCreate(&x));
+  try {
+    for (int i = 0; i < b; ++i, ++g_host) {
+      const StepRef sr{nullptr, g_host, nullptr};
+      CK(cudaEventRecord(ev[2 * i], stream));
+      launch_deliver(dev, tune_grid[(size_t)((tune_done + i) % C)], sr, stream);
+      CK(cudaEventRecord(ev[2 * i + 1], stream));
+      launch_update(dev, sr, stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(ev[2 * (size_t)b - 1]));
+    for (int i = 0; i < b; ++i) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+      tune_ms[(size_t)((tune_done + i) % C)] += ms;
+    }
+  } catch (...) {
+    for (auto& x : ev) cudaEventDestroy(x);
+    throw;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  tune_done += b;
+  if (tune_done == total) {
+    int best = 0;
+    for (int c = 1; c < C; ++c)
+      if (tune_ms[(size_t)c] < tune_ms[(size_t)best]) best = c;
+    if (tune_grid[(size_t)best] != del_grid) {
+      del_grid = tune_grid[(size_t)best];
+      if (gexec) {
+        CK(cudaGraphExecDestroy(gexec));
+        gexec = nullptr;
+      }
+    }
+    tune_pending = false;
+  }
+  return b;
+}
+
+// n steps with the current delivery grid: whole chunks from the captured
+// graph, the rest as direct launches
+void Engine::run_plain(int64_t n) {
   if (n >= kChunk) {
     if (!gexec) capture();
     launch_set_base(base.p, g_host, stream);
@@ -476,8 +551,6 @@ void Engine::step(int64_t n) {
     launch_deliver(dev, del_grid, sr, stream);
     launch_update(dev, sr, stream);
   }
-  launch_close(dev, g_host, stream);
-  CK(cudaGetLastError());
 }
 
 void Engine::step_timed(int64_t n, double* ms) {
@@ -607,6 +680,7 @@ int dbnet_options_default(dbnet_options_t* o) {
   o->precision = 32;
   o->raster_capacity = 0;
   o->bold_capacity = 4096;
+  o->autotune_at = 2000;
   return DBNET_OK;
 }
 
@@ -779,6 +853,8 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     out->max_delay = ih.graph->max_delay;
     out->packed_edges = ih.graph->packed ? 1 : 0;
     out->weights_rounded = ih.graph->rounded ? 1 : 0;
+    out->deliver_blocks = e.del_grid;
+    out->autotuned = (!e.tune_pending && !e.tune_grid.empty()) ? 1 : 0;
   });
 }
 

@@ -121,6 +121,15 @@ struct Engine {
   EngineDev dev{};
   cudaGraphExec_t gexec = nullptr;
   int del_grid = 0;
+  // delivery-grid autotuner: from iteration tune_at on, kTuneRounds rounds
+  // over the candidate grids, each step's delivery timed by CUDA events;
+  // the fastest total wins and the step graph is captured again
+  static constexpr int kTuneRounds = 16;
+  bool tune_pending = false;
+  unsigned long long tune_at = 0;
+  int tune_done = 0;                  // steps timed so far
+  std::vector<int> tune_grid;         // candidates
+  std::vector<double> tune_ms;        // summed delivery time per candidate
   int32_t n_tiles = 0, total_R = 0, shift_S = 16;
   int64_t stride = 0;
   bool poisoned = false;
@@ -133,6 +142,8 @@ struct Engine {
   void check() const;
   void capture();
   void step(int64_t n);
+  void run_plain(int64_t n);
+  int64_t tune_steps(int64_t n);
   void step_timed(int64_t n, double* ms);
   void sync();
   InstDyn read_dyn(int k);

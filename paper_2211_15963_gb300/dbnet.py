@@ -54,13 +54,14 @@ class dbnet_options_t(ctypes.Structure):
                 ("bw_kappa", _d), ("bw_gamma", _d), ("bw_tau", _d), ("bw_alpha", _d),
                 ("bw_rho", _d), ("bw_V0", _d), ("seed", _u64), ("net_id", _u64),
                 ("fixed_shift", _i32), ("precision", _i32), ("raster_capacity", _i64),
-                ("bold_capacity", _i64)]
+                ("bold_capacity", _i64), ("autotune_at", _i64)]
 
 
 class dbnet_stats_t(ctypes.Structure):
     _fields_ = [("step", _i64), ("spikes", _i64), ("events", _i64), ("raster_len", _i64),
                 ("raster_dropped", _i64), ("bold_samples", _i64), ("fixed_shift", _i32),
-                ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32)]
+                ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32),
+                ("deliver_blocks", _i32), ("autotuned", _i32)]
 
 
 class dbnet_device_graph_t(ctypes.Structure):
@@ -469,6 +470,16 @@ class Ensemble:
     def member_spikes(self, m: int):
         v = ens_member(self.h, m)
         return dbnet_read_spikes(v)
+
+    def member_stats(self, m: int) -> dict:
+        return dbnet_stats(ens_member(self.h, m))
+
+    def stats(self) -> dict:
+        """Ensemble totals: events (engine-wide) and spikes summed over members."""
+        s = [self.member_stats(m) for m in range(self.M)]
+        out = dict(s[0])
+        out["spikes"] = sum(x["spikes"] for x in s)
+        return out
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -46,6 +46,7 @@ def test_strerror_and_defaults(lib):
     o = dbnet.dbnet_options_default()
     assert o.dt_ms == 0.1 and o.bin_ms == 1.0 and o.tr_ms == 800.0 and o.precision == 32
     assert abs(o.bw_rho - 0.34) < 1e-15 and o.bold_capacity == 4096
+    assert o.autotune_at == 2000
 
 
 def _tiny_graph():
@@ -85,6 +86,7 @@ def test_host_validation_rejects_malformed_inputs(lib):
     _expect(dbnet.DBNET_EINVAL, g, tr_ms=800.5)
     _expect(dbnet.DBNET_EUNSUPPORTED, g, precision=64)
     _expect(dbnet.DBNET_EINVAL, g, fixed_shift=31)
+    _expect(dbnet.DBNET_EINVAL, g, autotune_at=-2)
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -253,3 +253,27 @@ def test_long_run_statistics_against_fp64_oracle(small_graph):
     assert abs(metrics.isi_cv(st, ids) - metrics.isi_cv(rs, rids)) < 0.02
     y, yo = net.bold()[:, 0], o.bold()[:, 0]
     assert metrics.pcc(y, yo) >= 0.99
+
+
+def test_autotuned_grid_gives_identical_results():
+    """The delivery-grid autotuner changes only the launch shape: a run that
+    tunes mid-way ends bit-identical to one that never tunes, and reports the
+    grid it kept."""
+    g = synth.make_graph([3000, 2000, 2500], 80, 41, d_within=(1, 30), d_cross=(30, 90))
+    p = synth.default_region_params()
+    tuned = _net(g, p, seed=5, autotune_at=150)
+    plain = _net(g, p, seed=5, autotune_at=-1)
+    for n in (100, 333, 700):  # tuning starts inside the second call
+        tuned.step(n)
+        plain.step(n)
+    st, sp = tuned.stats(), plain.stats()
+    assert st["autotuned"] == 1 and sp["autotuned"] == 0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert st["deliver_blocks"] in [sms * k for k in (1, 2, 3, 4)]
+    assert st["events"] == sp["events"] and st["spikes"] == sp["spikes"]
+    _assert_same_state(tuned, plain, "autotuned")
+    a, b = tuned.spikes(), plain.spikes()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(tuned.bold(), plain.bold())
+    tuned.close()
+    plain.close()
