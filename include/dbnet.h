@@ -309,6 +309,125 @@ int dbnet_run_noalloc(const dbnet_device_graph_t* graph, const dbnet_region_para
                       int64_t raster_cap, int64_t* n_spikes, int64_t* n_events,
                       void* cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Request server: continuous batching of simulation requests on one GPU.
+ *
+ * The paper runs one brain model per machine; it has no request server.
+ * This is the serving form of the same step: many independent networks
+ * (requests) share one engine, and every update and delivery launch covers
+ * all requests resident at that moment.  A request is admitted when a
+ * request slot, contiguous neuron tiles, region slots and room in the
+ * server's device arena are free; until then it waits in a queue (first
+ * fit over the oldest queued requests).  Its state stays resident until it
+ * has run its n_steps; its results are then copied to the host, and its
+ * slot, tiles and memory return to the pool once D more iterations have
+ * completed (no spike of it is still in flight).  Requests do not interact:
+ * each gives the same spikes, state and BOLD as the same network created
+ * alone with dbnet_create and the same seed, net_id and options.
+ * All device memory of requests comes from one arena allocated at
+ * dbsrv_create, so admission and retirement never allocate or free device
+ * memory.  A handle is not thread-safe.
+ * ------------------------------------------------------------------- */
+typedef struct dbsrv dbsrv_t;
+
+typedef struct {
+  int64_t max_neurons;    /* neuron capacity (whole tiles of 1024) */
+  int32_t max_requests;   /* request slots (running or cooling down) */
+  int32_t max_regions;    /* region slots */
+  int32_t max_delay;      /* longest delay any request may use, steps (1..255) */
+  int32_t chunk_steps;    /* Euler steps per scheduling round */
+  int64_t arena_bytes;    /* device memory for the requests' graphs and buffers */
+  int32_t max_inflight;   /* rounds enqueued ahead of the host */
+  int32_t reserved;
+  dbnet_options_t run;    /* dt, bin, TR, z_scale, hemodynamic constants,
+                             fixed_shift, autotune_at, precision; seed, net_id
+                             and capacities come with each request */
+} dbsrv_options_t;
+
+typedef struct {
+  int64_t n_steps;        /* Euler steps to run (>= 1) */
+  uint64_t seed, net_id;  /* Philox key, as in dbnet_options_t */
+  uint64_t graph_key;     /* non-zero: requests with the same key share one
+                             device copy of the graph (the caller asserts the
+                             graphs are identical); 0: a private copy */
+  int64_t bold_capacity;  /* BOLD samples kept; 0 = all of n_steps */
+  int64_t raster_capacity;/* spikes kept (0 = none) */
+} dbsrv_request_t;
+
+#define DBSRV_QUEUED 0
+#define DBSRV_RUNNING 1
+#define DBSRV_DONE 2
+#define DBSRV_FAILED 3
+
+typedef struct {
+  int32_t state;          /* DBSRV_* */
+  int32_t error;          /* status code when FAILED */
+  int64_t steps;          /* steps completed, as known to the host */
+  int64_t spikes;         /* spikes emitted (final when DONE) */
+  int64_t bold_samples;   /* BOLD samples held (when DONE) */
+  int64_t raster_len;     /* spikes held (when DONE) */
+  double queued_s;        /* submit -> admission (wall clock) */
+  double run_s;           /* admission -> results on the host */
+  double latency_s;       /* submit -> results on the host */
+} dbsrv_status_t;
+
+typedef struct {
+  int64_t iterations;     /* engine iterations completed on the device */
+  int64_t events;         /* synaptic events applied, all requests */
+  int32_t running, queued, cooling, done;
+  int64_t arena_used, arena_bytes;
+  int32_t tiles_in_use, tile_extent;
+} dbsrv_stats_t;
+
+/* Defaults: 8,388,608 neurons, 64 requests, 1,024 regions, delays <= 255,
+ * 256 steps per round, a 64 GiB arena, 2 rounds in flight,
+ * dbnet_options_default() for the run options. */
+int dbsrv_options_default(dbsrv_options_t* o);
+
+/* Allocate the pool (neuron state, spike rings, arena) on the current
+ * device.  cuda_stream: the stream every step runs on (NULL: its own).
+ * DBNET_EINVAL for bad options, DBNET_ENOMEM when the pool does not fit. */
+int dbsrv_create(const dbsrv_options_t* options, void* cuda_stream, dbsrv_t** out);
+
+/* Queue a request.  graph and params follow dbnet_create; params [R].  The
+ * graph's host arrays must stay valid until the request leaves the queue
+ * (dbsrv_poll reports RUNNING, DONE or FAILED); params are copied now.
+ * Host checks only (cheap): DBNET_EINVAL for malformed arguments, DBNET_ERANGE
+ * when the request could never fit the pool.  Problems found on the device
+ * at admission (bad edges, a delay over max_delay) fail that request alone:
+ * state FAILED with the status code.  *id receives the request id (>= 1). */
+int dbsrv_submit(dbsrv_t* s, const dbnet_graph_t* graph, const dbnet_region_params_t* params,
+                 const dbsrv_request_t* request, int64_t* id);
+
+/* One scheduling round: note the rounds the device has finished, copy the
+ * results of requests that have run their steps, return cooled slots to the
+ * pool, admit queued requests that fit (their graphs are copied on a second
+ * stream while the device keeps stepping), and enqueue chunk_steps steps of
+ * every resident request.  Blocks only when max_inflight rounds are already
+ * enqueued, until the oldest finishes.  out may be NULL. */
+int dbsrv_pump(dbsrv_t* s, dbsrv_stats_t* out);
+
+/* Pump until no request is queued, running or cooling down. */
+int dbsrv_drain(dbsrv_t* s);
+
+int dbsrv_poll(dbsrv_t* s, int64_t id, dbsrv_status_t* out);
+
+/* Results of a DONE request: BOLD samples [n][R] (as dbnet_read_bold) and
+ * recorded spikes sorted by (step, id) (as dbnet_read_spikes).
+ * DBNET_ESTATE when the request is not DONE, DBNET_ERANGE when cap is short. */
+int dbsrv_read_bold(dbsrv_t* s, int64_t id, double* y, int64_t cap_samples, int64_t* n_out);
+int dbsrv_read_spikes(dbsrv_t* s, int64_t id, int32_t* step, int32_t* nid, int64_t cap,
+                      int64_t* n_out);
+
+/* Forget a DONE or FAILED request, or cancel a QUEUED one (DBNET_ESTATE for
+ * a running request). */
+int dbsrv_release(dbsrv_t* s, int64_t id);
+
+int dbsrv_stats(dbsrv_t* s, dbsrv_stats_t* out);
+
+/* Waits for the device, then frees everything. */
+void dbsrv_destroy(dbsrv_t* s);
+
 #ifdef __cplusplus
 }
 #endif

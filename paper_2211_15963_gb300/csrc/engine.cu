@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -28,6 +29,7 @@
 namespace dbn {
 
 thread_local std::string g_last_error;
+thread_local Arena* g_arena = nullptr;
 
 // ---------------------------------------------------------------- graph ----
 std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
@@ -222,15 +224,7 @@ void check_options(const dbnet_options_t& o) {
 
 // --------------------------------------------------------------- engine ----
 void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
-  if (user_stream) {
-    stream = (cudaStream_t)user_stream;
-    own_stream = false;
-  } else {
-    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-    own_stream = true;
-  }
   const int n = (int)specs.size();
-  inst.resize(n);
   // fixed-point scale shared by the engine
   double wext_max = 0.0;
   for (const auto& sp : specs)
@@ -238,30 +232,44 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   int S = 16;
   for (int k = 0; k < n; ++k) S = std::min(S, choose_shift(*specs[k].graph, wext_max, specs[0].opt.fixed_shift));
   shift_S = S;
-  // layout
+  // layout: instances end to end, each on whole tiles
   int64_t tiles = 0;
-  int32_t rbase = 0;
-  int32_t dmax_all = 1;
-  for (int k = 0; k < n; ++k) {
-    const InstSpec& sp = specs[k];
-    InstHost& ih = inst[k];
-    const GraphDev& g = *sp.graph;
-    ih.graph = sp.graph;
-    ih.first_tile = (int32_t)tiles;
-    ih.n_tiles = (g.N + kTile - 1) / kTile;
-    tiles += ih.n_tiles;
-    ih.rbase = rbase;
-    rbase += g.R;
-    for (int32_t r = 0; r < g.R; ++r)
-      ih.rc_h.push_back(region_const(sp.params[r], sp.opt.dt_ms, S, g.ro_h[r], g.ro_h[r + 1],
-                                     g.ro_h[r] + g.nexc_h[r]));
-    dmax_all = std::max(dmax_all, g.max_delay);
-    ih.opt = sp.opt;
-    ih.net_id = sp.net_id;
+  int32_t regions = 0, dmax_all = 1;
+  for (const auto& sp : specs) {
+    tiles += (sp.graph->N + kTile - 1) / kTile;
+    regions += sp.graph->R;
+    dmax_all = std::max(dmax_all, sp.graph->max_delay);
   }
-  n_tiles = (int32_t)tiles;
-  total_R = rbase;
+  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream);
+  int64_t t = 0;
+  int32_t r = 0;
+  for (int k = 0; k < n; ++k) {
+    place(k, specs[k], (int32_t)t, r, S, LLONG_MAX);
+    t += (specs[k].graph->N + kTile - 1) / kTile;
+    r += specs[k].graph->R;
+  }
+  set_extent((int32_t)tiles, regions);
+  CK(cudaStreamSynchronize(stream));
+}
+
+void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
+                       const dbnet_options_t& common, void* user_stream) {
+  if (user_stream) {
+    stream = (cudaStream_t)user_stream;
+    own_stream = false;
+  } else {
+    CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  if (n_inst < 1 || tiles < 1 || regions < 1) raise(DBNET_EINVAL, "empty engine");
+  if (D < 2 || D > 256) raise(DBNET_EINVAL, "delays must be 1..255 steps");
   stride = tiles * kTile;
+  if (stride >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "too many neurons in one engine");
+  cap_tiles = (int32_t)tiles;
+  cap_R = regions;
+  cap_inst = n_inst;
+  inst.clear();
+  inst.resize((size_t)n_inst);
 
   V.alloc(stride);
   J.alloc(4 * stride);
@@ -271,90 +279,37 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
   CK(cudaMemsetAsync(ref.p, 0, stride, stream));
   CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * stride, stream));
-  std::vector<int4> tile_info_h((size_t)tiles);
-  std::vector<int32_t> region_inst_h((size_t)total_R);
-  std::vector<InstDesc> desc_h((size_t)n);
-  for (int k = 0; k < n; ++k) {
-    InstHost& ih = inst[k];
-    const GraphDev& g = *ih.graph;
-    for (int t = 0; t < ih.n_tiles; ++t) {
-      // regions touched by the tile's neurons [t*kTile, min((t+1)*kTile, N))
-      const int32_t lo = t * kTile, hi = std::min((t + 1) * kTile, g.N) - 1;
-      const int32_t r0 = (int32_t)(std::upper_bound(g.ro_h.begin(), g.ro_h.end(), lo) - g.ro_h.begin()) - 1;
-      const int32_t r1 = (int32_t)(std::upper_bound(g.ro_h.begin(), g.ro_h.end(), hi) - g.ro_h.begin()) - 1;
-      tile_info_h[(size_t)(ih.first_tile + t)] = make_int4(k, r0, r1 - r0 + 1, 0);
-    }
-    for (int32_t r = 0; r < g.R; ++r) region_inst_h[(size_t)(ih.rbase + r)] = k;
-    ih.rc.alloc(g.R);
-    CK(cudaMemcpyAsync(ih.rc.p, ih.rc_h.data(), sizeof(RegionConst) * g.R, cudaMemcpyHostToDevice, stream));
-    const dbnet_options_t& o = ih.opt;
-    ih.bold.alloc(std::max<int64_t>(o.bold_capacity, 1) * g.R);
-    if (o.raster_capacity > 0) {
-      ih.raster_step.alloc(o.raster_capacity);
-      ih.raster_id.alloc(o.raster_capacity);
-    }
-    InstDesc& d = desc_h[(size_t)k];
-    std::memset(&d, 0, sizeof(d));
-    d.row_ptr = g.row_ptr.p;
-    d.rec = g.rec.p;
-    d.col = nullptr;
-    d.w = nullptr;
-    d.delay = nullptr;
-    d.seg = g.seg.p;
-    d.seg_kind = g.seg_kind;
-    d.dmax = g.max_delay;
-    d.seg_stride = g.seg_stride;
-    d.region_offsets = g.ro.p;
-    d.rc = ih.rc.p;
-    d.bold = ih.bold.p;
-    d.raster_step = ih.raster_step.p;
-    d.raster_id = ih.raster_id.p;
-    d.base = (int64_t)ih.first_tile * kTile;
-    d.raster_cap = o.raster_capacity;
-    d.bold_cap = o.bold_capacity;
-    d.seed = o.seed;
-    d.net_id = ih.net_id;
-    d.N = g.N;
-    d.R = g.R;
-    d.rbase = ih.rbase;
-    d.shift = 32;
-    d.tmask = 0xFFFFFFFFu;
-    d.two_S = std::ldexp(1.0f, S);
-    d.inv_two_S = std::ldexp(1.0f, -S);
-    d.spb = (int32_t)std::lrint(o.bin_ms / o.dt_ms);
-    d.bins_per_tr = (int32_t)std::lrint(o.tr_ms / o.bin_ms);
-    d.h_bw = o.bin_ms * 1e-3;
-    d.z_scale = o.z_scale;
-    d.kappa = o.bw_kappa;
-    d.gamma = o.bw_gamma;
-    d.tau = o.bw_tau;
-    d.alpha = o.bw_alpha;
-    d.rho = o.bw_rho;
-    d.V0 = o.bw_V0;
-    ih.desc = d;
-  }
-  desc.alloc(n);
-  dyn.alloc(n);
-  tile_info.alloc(std::max<int64_t>(tiles, 1));
-  closed.alloc(std::max(total_R, 1));
-  region_inst.alloc(std::max(total_R, 1));
-  cnt.alloc(std::max(total_R, 1));
-  bw.alloc(4 * std::max(total_R, 1));
-  ylast.alloc(std::max(total_R, 1));
+  desc.alloc(n_inst);
+  dyn.alloc(n_inst);
+  tile_info.alloc(tiles);
+  closed.alloc(regions);
+  region_inst.alloc(regions);
+  cnt.alloc(regions);
+  bw.alloc(4 * (int64_t)regions);
+  ylast.alloc(regions);
+  CK(cudaMemsetAsync(desc.p, 0, sizeof(InstDesc) * n_inst, stream));
+  CK(cudaMemsetAsync(dyn.p, 0, sizeof(InstDyn) * n_inst, stream));  // inactive
+  // host sources of the asynchronous copies that clear tiles and counters;
+  // they live as long as the engine
+  no_tiles_h.assign((size_t)tiles, make_int4(-1, 0, 0, 0));
+  zero_dyn_h.assign((size_t)n_inst, InstDyn{});
+  CK(cudaMemcpyAsync(tile_info.p, no_tiles_h.data(), sizeof(int4) * tiles, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(region_inst.p, 0xFF, sizeof(int32_t) * regions, stream));  // -1: unused
+  CK(cudaMemsetAsync(closed.p, 0, sizeof(long long) * regions, stream));
+  CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * regions, stream));
+  CK(cudaMemsetAsync(bw.p, 0, sizeof(double) * 4 * regions, stream));
+  CK(cudaMemsetAsync(ylast.p, 0, sizeof(double) * regions, stream));
   // spike ring: a slot per step of the longest delay, each able to hold every neuron
-  const int32_t D = dmax_all + 1;
-  if (stride >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "too many neurons in one engine");
   hist.alloc((int64_t)D * stride);
   hcount.alloc(D);
+  CK(cudaMemsetAsync(hcount.p, 0, sizeof(uint32_t) * D, stream));
   // delay-major segment ring: room for seg_cap spikes per step -- a 64th of
-  // the neurons (at least 4096), within a sixteenth of the free memory;
-  // every instance with a u16 table uses it, and a step's spikes beyond
-  // seg_cap take the direct path
-  bool any16 = false;
-  for (int k = 0; k < n; ++k) any16 = any16 || inst[k].graph->seg_kind == kSeg16;
+  // the neurons (at least 4096), within a sixteenth of the free memory; a
+  // step's spikes beyond seg_cap (and instances with u32 tables) take the
+  // direct path
+  const int32_t dcap = D - 1;
   int64_t seg_cap = 0;
-  const int32_t dcap = dmax_all;
-  if (any16) {
+  {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     const int64_t budget = (int64_t)(free_b / 16);
@@ -370,25 +325,6 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   base.alloc(2);
   events.alloc(1);
   flags.alloc(1);
-  std::vector<InstDyn> dyn_h((size_t)n);
-  std::memset(dyn_h.data(), 0, sizeof(InstDyn) * n);
-  for (auto& x : dyn_h) x.active = 1;
-  std::vector<double> bw_h((size_t)total_R * 4);
-  for (int32_t r = 0; r < total_R; ++r) {
-    bw_h[(size_t)r * 4 + 0] = 0.0;
-    bw_h[(size_t)r * 4 + 1] = 1.0;
-    bw_h[(size_t)r * 4 + 2] = 1.0;
-    bw_h[(size_t)r * 4 + 3] = 1.0;
-  }
-  CK(cudaMemcpyAsync(desc.p, desc_h.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, stream));
-  CK(cudaMemcpyAsync(dyn.p, dyn_h.data(), sizeof(InstDyn) * n, cudaMemcpyHostToDevice, stream));
-  CK(cudaMemcpyAsync(tile_info.p, tile_info_h.data(), sizeof(int4) * tiles, cudaMemcpyHostToDevice, stream));
-  CK(cudaMemsetAsync(closed.p, 0, sizeof(long long) * std::max(total_R, 1), stream));
-  CK(cudaMemcpyAsync(region_inst.p, region_inst_h.data(), sizeof(int32_t) * total_R, cudaMemcpyHostToDevice, stream));
-  CK(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * std::max(total_R, 1), stream));
-  CK(cudaMemcpyAsync(bw.p, bw_h.data(), sizeof(double) * 4 * total_R, cudaMemcpyHostToDevice, stream));
-  CK(cudaMemsetAsync(ylast.p, 0, sizeof(double) * std::max(total_R, 1), stream));
-  CK(cudaMemsetAsync(hcount.p, 0, sizeof(uint32_t) * D, stream));
   CK(cudaMemsetAsync(base.p, 0, sizeof(unsigned long long) * 2, stream));
   CK(cudaMemsetAsync(events.p, 0, sizeof(unsigned long long), stream));
   CK(cudaMemsetAsync(flags.p, 0, sizeof(unsigned), stream));
@@ -417,12 +353,13 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
   dev.D = D;
   dev.events = events.p;
   dev.flags = flags.p;
-  dev.n_inst = n;
-  dev.n_tiles = n_tiles;
-  dev.total_R = total_R;
-  for (int k = 0; k < n; ++k) launch_init_state(dev, k, inst[k].n_tiles, inst[k].first_tile, stream);
+  dev.n_inst = n_inst;
+  dev.n_tiles = 0;
+  dev.total_R = 0;
+  n_tiles = 0;
+  total_R = 0;
   del_grid = deliver_grid();
-  if (specs[0].opt.autotune_at >= 0) {
+  if (common.autotune_at >= 0) {
     int dev_id = 0, sms = 0;
     CK(cudaGetDevice(&dev_id));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
@@ -430,11 +367,135 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     if (tune_grid.size() > 1) {
       tune_ms.assign(tune_grid.size(), 0.0);
       tune_pending = true;
-      tune_at = (unsigned long long)specs[0].opt.autotune_at;
+      tune_at = (unsigned long long)common.autotune_at;
     }
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(stream));
+}
+
+void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase, int S,
+                   long long n_end) {
+  const GraphDev& g = *sp.graph;
+  const int32_t nt = (g.N + kTile - 1) / kTile;
+  if (k < 0 || k >= cap_inst || first_tile < 0 || first_tile + nt > cap_tiles || rbase < 0 ||
+      rbase + g.R > cap_R)
+    raise(DBNET_EINVAL, "instance placement outside the engine's capacity");
+  if (g.max_delay >= dev.D) raise(DBNET_EINVAL, "a delay is longer than the engine's ring");
+  InstHost& ih = inst[(size_t)k];
+  ih = InstHost{};
+  ih.graph = sp.graph;
+  ih.first_tile = first_tile;
+  ih.n_tiles = nt;
+  ih.rbase = rbase;
+  ih.opt = sp.opt;
+  ih.net_id = sp.net_id;
+  for (int32_t r = 0; r < g.R; ++r)
+    ih.rc_h.push_back(region_const(sp.params[r], sp.opt.dt_ms, S, g.ro_h[r], g.ro_h[r + 1],
+                                   g.ro_h[r] + g.nexc_h[r]));
+  ih.rc.alloc(g.R);
+  CK(cudaMemcpyAsync(ih.rc.p, ih.rc_h.data(), sizeof(RegionConst) * g.R, cudaMemcpyHostToDevice, stream));
+  const dbnet_options_t& o = ih.opt;
+  ih.bold.alloc(std::max<int64_t>(o.bold_capacity, 1) * g.R);
+  if (o.raster_capacity > 0) {
+    ih.raster_step.alloc(o.raster_capacity);
+    ih.raster_id.alloc(o.raster_capacity);
+  }
+  InstDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.row_ptr = g.row_ptr.p;
+  d.rec = g.rec.p;
+  d.col = nullptr;
+  d.w = nullptr;
+  d.delay = nullptr;
+  d.seg = g.seg.p;
+  d.seg_kind = g.seg_kind;
+  d.dmax = g.max_delay;
+  d.seg_stride = g.seg_stride;
+  d.region_offsets = g.ro.p;
+  d.rc = ih.rc.p;
+  d.bold = ih.bold.p;
+  d.raster_step = ih.raster_step.p;
+  d.raster_id = ih.raster_id.p;
+  d.base = (int64_t)first_tile * kTile;
+  d.raster_cap = o.raster_capacity;
+  d.bold_cap = o.bold_capacity;
+  d.seed = o.seed;
+  d.net_id = ih.net_id;
+  d.g0 = g_host;
+  d.n_end = n_end;
+  d.N = g.N;
+  d.R = g.R;
+  d.rbase = rbase;
+  d.shift = 32;
+  d.tmask = 0xFFFFFFFFu;
+  d.two_S = std::ldexp(1.0f, S);
+  d.inv_two_S = std::ldexp(1.0f, -S);
+  d.spb = (int32_t)std::lrint(o.bin_ms / o.dt_ms);
+  d.bins_per_tr = (int32_t)std::lrint(o.tr_ms / o.bin_ms);
+  d.h_bw = o.bin_ms * 1e-3;
+  d.z_scale = o.z_scale;
+  d.kappa = o.bw_kappa;
+  d.gamma = o.bw_gamma;
+  d.tau = o.bw_tau;
+  d.alpha = o.bw_alpha;
+  d.rho = o.bw_rho;
+  d.V0 = o.bw_V0;
+  ih.desc = d;
+  // device tables: descriptor, counters, tiles and region slots
+  InstDyn dy;
+  std::memset(&dy, 0, sizeof(dy));
+  dy.active = 1;
+  std::vector<int4> ti((size_t)nt);
+  for (int32_t t = 0; t < nt; ++t) {
+    // regions touched by the tile's neurons [t*kTile, min((t+1)*kTile, N))
+    const int32_t lo = t * kTile, hi = std::min((t + 1) * kTile, g.N) - 1;
+    const int32_t r0 = (int32_t)(std::upper_bound(g.ro_h.begin(), g.ro_h.end(), lo) - g.ro_h.begin()) - 1;
+    const int32_t r1 = (int32_t)(std::upper_bound(g.ro_h.begin(), g.ro_h.end(), hi) - g.ro_h.begin()) - 1;
+    ti[(size_t)t] = make_int4(k, r0, r1 - r0 + 1, 0);
+  }
+  ih.stage_ti = std::move(ti);
+  ih.stage_ri.assign((size_t)g.R, k);
+  ih.stage_bw.assign((size_t)g.R * 4, 1.0);
+  for (int32_t r = 0; r < g.R; ++r) ih.stage_bw[(size_t)r * 4] = 0.0;  // s = 0, f = v = q = 1
+  CK(cudaMemcpyAsync(desc.p + k, &ih.desc, sizeof(InstDesc), cudaMemcpyHostToDevice, stream));
+  ih.stage_dyn = dy;
+  CK(cudaMemcpyAsync(dyn.p + k, &ih.stage_dyn, sizeof(InstDyn), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(tile_info.p + first_tile, ih.stage_ti.data(), sizeof(int4) * nt,
+                     cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(region_inst.p + rbase, ih.stage_ri.data(), sizeof(int32_t) * g.R,
+                     cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(bw.p + 4 * (int64_t)rbase, ih.stage_bw.data(), sizeof(double) * 4 * g.R,
+                     cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(cnt.p + rbase, 0, sizeof(int32_t) * g.R, stream));
+  CK(cudaMemsetAsync(ylast.p + rbase, 0, sizeof(double) * g.R, stream));
+  CK(cudaMemsetAsync(closed.p + rbase, 0, sizeof(long long) * g.R, stream));
+  launch_init_state(dev, k, nt, first_tile, stream);
+  CK(cudaGetLastError());
+}
+
+void Engine::vacate(int k) {
+  InstHost& ih = inst[(size_t)k];
+  if (!ih.graph) return;
+  CK(cudaMemcpyAsync(dyn.p + k, zero_dyn_h.data() + k, sizeof(InstDyn), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(tile_info.p + ih.first_tile, no_tiles_h.data() + ih.first_tile,
+                     sizeof(int4) * ih.n_tiles, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(region_inst.p + ih.rbase, 0xFF, sizeof(int32_t) * ih.graph->R, stream));
+  ih = InstHost{};  // its staged tables were copied when it was placed, long before
+}
+
+void Engine::set_extent(int32_t tiles, int32_t regions) {
+  if (tiles == n_tiles && regions == total_R) return;
+  if (tiles < 0 || tiles > cap_tiles || regions < 0 || regions > cap_R)
+    raise(DBNET_EINVAL, "extent outside the engine's capacity");
+  if (gexec) {
+    CK(cudaStreamSynchronize(stream));
+    CK(cudaGraphExecDestroy(gexec));
+    gexec = nullptr;
+  }
+  n_tiles = tiles;
+  total_R = regions;
+  dev.n_tiles = tiles > 0 ? tiles : 1;  // one (unused) block still advances the iteration word
+  dev.total_R = regions;
 }
 
 Engine::~Engine() {

@@ -76,6 +76,7 @@ struct InstDesc {
   int64_t bold_cap;
   uint64_t seed, net_id;
   unsigned long long g0;         // engine iteration at which this instance's step 0 ran
+  long long n_end;               // steps it runs: later iterations leave it unchanged
   int32_t N, R, rbase, shift;
   uint32_t tmask;
   float two_S, inv_two_S;

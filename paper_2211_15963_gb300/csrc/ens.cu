@@ -234,11 +234,6 @@ __global__ void k_walk_rescale(double* theta, const double* xi, const double* ba
   rc[r].g[2] = (float)(base_g[2 * r + 1] * exp(tg));
 }
 
-__global__ void k_ypred_mean(const double* mu, double* out, int R) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < R) out[r] = mu[kB * r + kY];
-}
-
 inline int blocks(int64_t n, int t = 128) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace

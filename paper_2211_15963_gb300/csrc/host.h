@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <iterator>
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -30,37 +32,133 @@ struct Error {
 
 extern thread_local std::string g_last_error;
 
-// Device allocation owned by its holder.
+// A sub-allocator over one device allocation (first fit, 256-byte granules,
+// neighbours merged on release).  Used by the request server, so that
+// admitting and retiring requests never calls cudaMalloc or cudaFree (the
+// latter waits for the whole device).  Not thread-safe.
+class Arena {
+ public:
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  ~Arena() {
+    if (base_) cudaFree(base_);
+  }
+  void init(int64_t bytes) {
+    bytes = round(bytes);
+    cudaError_t e = cudaMalloc((void**)&base_, (size_t)bytes);
+    if (e != cudaSuccess) {
+      base_ = nullptr;
+      cudaGetLastError();
+      raise(e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,
+            "cudaMalloc of the " + std::to_string(bytes) + "-byte request arena: " +
+                cudaGetErrorString(e));
+    }
+    size_ = bytes;
+    free_.clear();
+    free_[0] = bytes;
+  }
+  void* take(int64_t bytes) {
+    bytes = round(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      const int64_t off = it->first, len = it->second;
+      free_.erase(it);
+      if (len > bytes) free_[off + bytes] = len - bytes;
+      used_ += bytes;
+      return base_ + off;
+    }
+    return nullptr;
+  }
+  void give(void* p, int64_t bytes) {
+    bytes = round(bytes);
+    int64_t off = static_cast<char*>(p) - base_;
+    used_ -= bytes;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && off + bytes == nx->first) {
+      bytes += nx->second;
+      nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        pv->second += bytes;
+        return;
+      }
+    }
+    free_[off] = bytes;
+  }
+  int64_t largest_free() const {
+    int64_t m = 0;
+    for (const auto& kv : free_) m = kv.second > m ? kv.second : m;
+    return m;
+  }
+  int64_t used() const { return used_; }
+  int64_t size() const { return size_; }
+  static int64_t round(int64_t b) { return (b + 255) / 256 * 256; }
+
+ private:
+  char* base_ = nullptr;
+  int64_t size_ = 0, used_ = 0;
+  std::map<int64_t, int64_t> free_;  // offset -> length
+};
+
+// The arena DevBuf::alloc draws from on this thread (nullptr: cudaMalloc).
+extern thread_local Arena* g_arena;
+struct ArenaScope {
+  Arena* prev;
+  explicit ArenaScope(Arena* a) : prev(g_arena) { g_arena = a; }
+  ~ArenaScope() { g_arena = prev; }
+};
+
+// Device allocation owned by its holder: cudaMalloc memory, or a range of
+// the arena that was current when it was allocated.
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   int64_t n = 0;
+  Arena* ar = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), ar(o.ar) { o.p = nullptr; o.n = 0; o.ar = nullptr; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { reset(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    if (this != &o) {
+      reset();
+      p = o.p; n = o.n; ar = o.ar;
+      o.p = nullptr; o.n = 0; o.ar = nullptr;
+    }
     return *this;
   }
   ~DevBuf() { reset(); }
   void alloc(int64_t count) {
     reset();
     if (count <= 0) return;
-    cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * (size_t)count);
+    const size_t bytes = sizeof(T) * (size_t)count;
+    if (g_arena) {
+      p = static_cast<T*>(g_arena->take((int64_t)bytes));
+      if (!p) raise(DBNET_ENOMEM, "request arena has no free range of " + std::to_string(bytes) + " bytes");
+      ar = g_arena;
+      n = count;
+      return;
+    }
+    cudaError_t e = cudaMalloc((void**)&p, bytes);
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
       raise(e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,
-            "cudaMalloc of " + std::to_string(sizeof(T) * (size_t)count) + " bytes: " +
-                cudaGetErrorString(e));
+            "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
     }
     n = count;
   }
   void reset() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (ar) ar->give(p, (int64_t)(sizeof(T) * (size_t)n));
+      else cudaFree(p);
+    }
     p = nullptr;
     n = 0;
+    ar = nullptr;
   }
 };
 
@@ -96,6 +194,11 @@ struct InstHost {
   dbnet_options_t opt;
   uint64_t net_id = 0;
   int32_t first_tile = 0, n_tiles = 0, rbase = 0;
+  // host sources of the placement copies (kept until the instance goes)
+  std::vector<int4> stage_ti;
+  std::vector<int32_t> stage_ri;
+  std::vector<double> stage_bw;
+  InstDyn stage_dyn{};
 };
 
 struct Engine {
@@ -130,15 +233,32 @@ struct Engine {
   int tune_done = 0;                  // steps timed so far
   std::vector<int> tune_grid;         // candidates
   std::vector<double> tune_ms;        // summed delivery time per candidate
-  int32_t n_tiles = 0, total_R = 0, shift_S = 16;
+  int32_t n_tiles = 0, total_R = 0, shift_S = 16;  // extents the kernels cover
   int64_t stride = 0;
+  int32_t cap_tiles = 0, cap_R = 0, cap_inst = 0;    // capacities
+  std::vector<int4> no_tiles_h;                       // copy sources that clear
+  std::vector<InstDyn> zero_dyn_h;                    //   tiles and counters
   bool poisoned = false;
   std::string poison_msg;
 
   Engine() = default;
   Engine(const Engine&) = delete;
   ~Engine();
+  // A fixed set of instances laid out end to end, sharing one fixed-point S.
   void init(const std::vector<InstSpec>& specs, void* user_stream);
+  // Empty capacity for instances placed later: every tile and region slot
+  // starts unused (the kernels skip it); D = longest delay + 1.
+  void init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
+                 const dbnet_options_t& common, void* user_stream);
+  // Put instance k on tiles [first_tile, +tiles of its graph) and region
+  // slots [rbase, +R): its constants, buffers and initial state; its step 0
+  // is the next iteration enqueued, and it stops after n_end steps.
+  void place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase, int S, long long n_end);
+  // Mark instance k's tiles and region slots unused and drop its buffers.
+  // The caller guarantees no enqueued kernel still reads them.
+  void vacate(int k);
+  // Tiles and region slots the kernels cover; a change re-captures the graph.
+  void set_extent(int32_t tiles, int32_t regions);
   void check() const;
   void capture();
   void step(int64_t n);

@@ -118,10 +118,11 @@ __device__ __forceinline__ unsigned long long step_of(const StepRef& sr) {
 // the bin ends a TR.
 __device__ void close_region(const EngineDev& e, int gr, unsigned long long g) {
   const int k = e.region_inst[gr];
-  if (!e.dyn[k].active) return;
+  if (k < 0 || !e.dyn[k].active) return;  // unused region slot, or retired
   const InstDesc& dk = e.insts[k];
   if (g <= dk.g0) return;
   const long long nk = (long long)(g - 1ull - dk.g0);  // step just completed
+  if (nk >= dk.n_end) return;                          // past the instance's last step
   if ((nk + 1) % dk.spb != 0) return;
   if (e.closed[gr] >= (long long)g) return;
   const int r = gr - dk.rbase;
@@ -164,12 +165,13 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
 
   const int4 ti = e.tile_info[tile];  // instance, first region, regions touched
-  const int inst = ti.x, r0 = ti.y, nr = ti.z;
-  const InstDesc& d = e.insts[inst];
   const unsigned long long g = step_of(sr);
   if (sr.next && threadIdx.x == 0) *sr.next = g + 1ull;
+  if (ti.x < 0) return;  // unused tile
+  const int inst = ti.x, r0 = ti.y, nr = ti.z;
+  const InstDesc& d = e.insts[inst];
   const long long n = (long long)(g - d.g0);
-  const bool active = e.dyn[inst].active != 0;
+  const bool active = e.dyn[inst].active != 0 && n < d.n_end;
   if (nr <= kTileRegions) {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(d.rc + r0);
     uint32_t* dst = reinterpret_cast<uint32_t*>(s_rc);
@@ -350,6 +352,7 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
       const uint32_t ent = e.hist[s1 * (unsigned long long)e.hist_cap + k];
       const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
       const int inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
+      if (inst < 0) continue;  // never for a listed spike: tiles are reused D steps late
       const InstDesc& dd = e.insts[inst];
       if (dd.seg_kind != kSeg16) continue;
       const int64_t j = gidx - dd.base;
@@ -424,15 +427,16 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
         const int mid = (lo + hi + 1) >> 1;
         if (s_pre[mid] <= t) lo = mid; else hi = mid - 1;
       }
-      const uint32_t d = (uint32_t)lo + 1u;
+      uint32_t d = (uint32_t)lo + 1u;
       const unsigned long long k = t - s_pre[lo];
       const unsigned long long slot = (g - d) % (unsigned long long)D;
       const uint32_t ent = e.hist[slot * (unsigned long long)e.hist_cap + k];
       const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
       cls = ent >> 31;
       inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
+      if (inst < 0) inst = 0, d = 0u;  // (as above) -- takes no edges
       const InstDesc& dd = e.insts[inst];
-      if ((int32_t)d <= dd.dmax) {
+      if (d >= 1u && (int32_t)d <= dd.dmax) {
         const int64_t j = gidx - dd.base;
         int64_t r0, a, b;
         if (dd.seg_kind == kSeg16 && d >= 2u && k < (unsigned long long)e.seg_cap) {

@@ -19,6 +19,8 @@
 // spike's due segment by binary search over its row's delays.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -242,6 +244,7 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     d.base = 0;
     d.seed = options->seed;
     d.net_id = options->net_id;
+    d.n_end = LLONG_MAX;  // runs every step it is given
     d.N = N;
     d.R = R;
     d.rbase = 0;

@@ -70,6 +70,32 @@ class dbnet_device_graph_t(ctypes.Structure):
                 ("delay", _vp)]
 
 
+class dbsrv_options_t(ctypes.Structure):
+    _fields_ = [("max_neurons", _i64), ("max_requests", _i32), ("max_regions", _i32),
+                ("max_delay", _i32), ("chunk_steps", _i32), ("arena_bytes", _i64),
+                ("max_inflight", _i32), ("reserved", _i32), ("run", dbnet_options_t)]
+
+
+class dbsrv_request_t(ctypes.Structure):
+    _fields_ = [("n_steps", _i64), ("seed", _u64), ("net_id", _u64), ("graph_key", _u64),
+                ("bold_capacity", _i64), ("raster_capacity", _i64)]
+
+
+class dbsrv_status_t(ctypes.Structure):
+    _fields_ = [("state", _i32), ("error", _i32), ("steps", _i64), ("spikes", _i64),
+                ("bold_samples", _i64), ("raster_len", _i64), ("queued_s", _d), ("run_s", _d),
+                ("latency_s", _d)]
+
+
+class dbsrv_stats_t(ctypes.Structure):
+    _fields_ = [("iterations", _i64), ("events", _i64), ("running", _i32), ("queued", _i32),
+                ("cooling", _i32), ("done", _i32), ("arena_used", _i64), ("arena_bytes", _i64),
+                ("tiles_in_use", _i32), ("tile_extent", _i32)]
+
+
+DBSRV_QUEUED, DBSRV_RUNNING, DBSRV_DONE, DBSRV_FAILED = 0, 1, 2, 3
+
+
 class dbens_enkf_t(ctypes.Structure):
     _fields_ = [("obs_var", _d), ("gamma", _d), ("rw_sigma", _d), ("theta_lo", _d),
                 ("theta_hi", _d), ("floor", _d), ("mode", _i32)]
@@ -99,6 +125,18 @@ _SIGS = {
     "ens_read": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "ens_member": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp)]),
     "ens_destroy": (None, [_vp]),
+    "dbsrv_options_default": (ctypes.c_int, [ctypes.POINTER(dbsrv_options_t)]),
+    "dbsrv_create": (ctypes.c_int, [ctypes.POINTER(dbsrv_options_t), _vp, ctypes.POINTER(_vp)]),
+    "dbsrv_submit": (ctypes.c_int, [_vp, ctypes.POINTER(dbnet_graph_t), _vp,
+                                    ctypes.POINTER(dbsrv_request_t), ctypes.POINTER(_i64)]),
+    "dbsrv_pump": (ctypes.c_int, [_vp, _vp]),
+    "dbsrv_drain": (ctypes.c_int, [_vp]),
+    "dbsrv_poll": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(dbsrv_status_t)]),
+    "dbsrv_read_bold": (ctypes.c_int, [_vp, _i64, _vp, _i64, ctypes.POINTER(_i64)]),
+    "dbsrv_read_spikes": (ctypes.c_int, [_vp, _i64, _vp, _vp, _i64, ctypes.POINTER(_i64)]),
+    "dbsrv_release": (ctypes.c_int, [_vp, _i64]),
+    "dbsrv_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dbsrv_stats_t)]),
+    "dbsrv_destroy": (None, [_vp]),
     "dbnet_run_noalloc": (ctypes.c_int, [ctypes.POINTER(dbnet_device_graph_t), _vp,
                                          ctypes.POINTER(dbnet_options_t), _i64, _vp, _vp, _vp,
                                          _vp, _vp, _i64, ctypes.POINTER(_i64),
@@ -485,6 +523,105 @@ class Ensemble:
         if getattr(self, "h", None):
             ens_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- serving ----
+def dbsrv_options_default(**over) -> dbsrv_options_t:
+    o = dbsrv_options_t()
+    _check(lib().dbsrv_options_default(ctypes.byref(o)), "dbsrv_options_default")
+    run = over.pop("run", None)
+    for k, v in over.items():
+        setattr(o, k, v)
+    if run:
+        r = options_from(run)
+        o.run = r
+    return o
+
+
+def _fields(st) -> dict:
+    return {k: getattr(st, k) for k, _ in type(st)._fields_}
+
+
+class Server:
+    """Owner of one dbsrv handle: a request server that batches independent
+    simulations on one GPU (continuous batching, admission by pool room)."""
+
+    def __init__(self, stream=None, **options):
+        self.opt = dbsrv_options_default(**options)
+        self.h = _vp()
+        _check(lib().dbsrv_create(ctypes.byref(self.opt), _stream(stream), ctypes.byref(self.h)),
+               "dbsrv_create")
+        self._keep = {}   # request id -> host arrays the server may still read
+        self._R = {}
+
+    def submit(self, graph, params, n_steps: int, *, seed: int = 1, net_id: int = 0,
+               graph_key: int = 0, bold_capacity: int = 0, raster_capacity: int = 0) -> int:
+        g, keep = graph_struct(graph)
+        P = params_array(params, int(graph.n_regions))
+        rq = dbsrv_request_t(int(n_steps), int(seed), int(net_id), int(graph_key),
+                             int(bold_capacity), int(raster_capacity))
+        rid = _i64()
+        _check(lib().dbsrv_submit(self.h, ctypes.byref(g), ctypes.cast(P, _vp), ctypes.byref(rq),
+                                  ctypes.byref(rid)), "dbsrv_submit")
+        self._keep[rid.value] = (g, keep, graph)
+        self._R[rid.value] = int(graph.n_regions)
+        return rid.value
+
+    def pump(self) -> dict:
+        st = dbsrv_stats_t()
+        _check(lib().dbsrv_pump(self.h, ctypes.byref(st)), "dbsrv_pump")
+        return _fields(st)
+
+    def drain(self) -> None:
+        _check(lib().dbsrv_drain(self.h), "dbsrv_drain")
+
+    def poll(self, rid: int) -> dict:
+        st = dbsrv_status_t()
+        _check(lib().dbsrv_poll(self.h, int(rid), ctypes.byref(st)), "dbsrv_poll")
+        d = _fields(st)
+        if d["state"] != DBSRV_QUEUED:
+            self._keep.pop(rid, None)   # admitted or failed: the arrays are no longer read
+        return d
+
+    def bold(self, rid: int) -> np.ndarray:
+        R = self._R[rid]
+        n = self.poll(rid)["bold_samples"]
+        y = np.zeros((max(n, 1), R))
+        got = _i64()
+        _check(lib().dbsrv_read_bold(self.h, int(rid), y.ctypes.data, int(n), ctypes.byref(got)),
+               "dbsrv_read_bold")
+        return y[:got.value]
+
+    def spikes(self, rid: int):
+        n = self.poll(rid)["raster_len"]
+        st = np.zeros(max(n, 1), dtype=np.int32)
+        ids = np.zeros(max(n, 1), dtype=np.int32)
+        got = _i64()
+        _check(lib().dbsrv_read_spikes(self.h, int(rid), st.ctypes.data, ids.ctypes.data, int(n),
+                                       ctypes.byref(got)), "dbsrv_read_spikes")
+        return st[:got.value], ids[:got.value]
+
+    def release(self, rid: int) -> None:
+        _check(lib().dbsrv_release(self.h, int(rid)), "dbsrv_release")
+        self._keep.pop(rid, None)
+        self._R.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = dbsrv_stats_t()
+        _check(lib().dbsrv_stats(self.h, ctypes.byref(st)), "dbsrv_stats")
+        return _fields(st)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().dbsrv_destroy(self.h)
+            self.h = None
+        self._keep = {}
 
     def __del__(self):
         try:

@@ -20,7 +20,7 @@ def _declared_functions():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b((?:dbnet|ens)_\w+)\s*\(", txt, flags=re.M)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b((?:dbnet|ens|dbsrv)_\w+)\s*\(", txt, flags=re.M)
     return sorted(set(names))
 
 
@@ -114,3 +114,15 @@ def test_ensemble_host_validation(lib):
     expect(dbnet.DBNET_EINVAL, theta_lo=1.0, theta_hi=0.0)
     expect(dbnet.DBNET_EINVAL, mode=7)
     expect(dbnet.DBNET_EINVAL, theta=np.full((3, 2, 2), np.nan))
+
+
+def test_server_host_validation(lib):
+    """dbsrv_create checks its options on the host before touching a device."""
+    for bad in (dict(max_requests=0), dict(max_delay=0), dict(max_delay=256),
+                dict(chunk_steps=0), dict(arena_bytes=1024), dict(max_neurons=0)):
+        with pytest.raises(dbnet.DbnetError) as ei:
+            dbnet.Server(**bad)
+        assert ei.value.code == dbnet.DBNET_EINVAL, bad
+    o = dbnet.dbsrv_options_default()
+    assert o.max_requests == 64 and o.max_delay == 255 and o.chunk_steps == 256
+    assert o.run.dt_ms == 0.1 and o.run.autotune_at == 2000
