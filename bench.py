@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--arrival-hz", type=float, default=4.0)
     ap.add_argument("--catalogue", type=int, default=16,
                     help="distinct request networks built before the stream starts")
+    ap.add_argument("--separate-requests", type=int, default=40)
     return ap.parse_args()
 
 
@@ -491,8 +492,169 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- serving workload ----
+# I_ext giving ~10 Hz at in-degree K (tune_drive on 50,000-neuron, 5-region
+# networks), interpolated linearly in log K -- log I_ext
+SERVE_DRIVE = [(100, 0.75084), (300, 2.36363), (1000, 4.88653)]
+
+
+def serve_drive(k):
+    import math
+    pts = SERVE_DRIVE
+    if k <= pts[0][0]:
+        return pts[0][1]
+    for (k0, v0), (k1, v1) in zip(pts, pts[1:]):
+        if k <= k1:
+            t = (math.log(k) - math.log(k0)) / (math.log(k1) - math.log(k0))
+            return math.exp(math.log(v0) + t * (math.log(v1) - math.log(v0)))
+    return pts[-1][1]
+
+
+def serving_trace(args):
+    """Poisson arrivals of requests drawn from the request distribution (size
+    log-uniform in [1e4, 1e6], in-degree U[100, 1000], 1-50 regions, 0.5-5 s
+    biological; the within-region share of the in-degree is capped at the
+    smallest region's size - 1).  To bound host generation time the networks come from a
+    catalogue of `--catalogue` draws built first; each request takes one of
+    them at random, with its own seed, net_id, drive and duration, and
+    uploads its own copy."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(synth.seed_for(3))
+    cat = []
+    for i in range(args.catalogue):
+        d = synth.serving_request(rng)
+        # 80 % of the in-degree within the region, at most the region's size - 1
+        kw = min(int(round(0.8 * d["k_in"])), min(d["sizes"]) - 1)
+        g = synth.make_graph(d["sizes"], d["k_in"], d["seed"], k_within=kw, d_within=(1, 50),
+                             d_cross=(50, 200))
+        p = synth.scale_for_degree(synth.default_region_params(I_ext=serve_drive(d["k_in"])), d["k_in"])
+        cat.append((g, [dict(p) for _ in d["sizes"]], d["k_in"]))
+    t = 0.0
+    reqs = []
+    for i in range(args.requests):
+        t += float(rng.exponential(1.0 / args.arrival_hz))
+        c = int(rng.integers(0, len(cat)))
+        bio_s = float(rng.uniform(0.5, 5.0))
+        reqs.append(dict(at=t, cat=c, n_steps=int(round(bio_s * STEPS_PER_BIO_S)), bio_s=bio_s,
+                         seed=int(rng.integers(1, 2**31)), net_id=i))
+    return cat, reqs
+
+
 def run_serving(args):
-    raise SystemExit("serving workload: not built yet")
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2211_15963_gb300 import dbnet
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    t_gen = time.perf_counter()
+    cat, reqs = serving_trace(args)
+    t_gen = time.perf_counter() - t_gen
+    srv = dbnet.Server(stream, max_neurons=8 << 20, max_requests=64, max_regions=4096,
+                       max_delay=200, chunk_steps=256, arena_bytes=96 << 30)
+    ids = [None] * len(reqs)
+    st = [None] * len(reqs)
+    pending = set()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0 = srv.stats()["events"]
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt]["at"] <= now:
+            r = reqs[nxt]
+            g, p, _ = cat[r["cat"]]
+            ids[nxt] = srv.submit(g, p, r["n_steps"], seed=r["seed"], net_id=r["net_id"])
+            pending.add(nxt)
+            nxt += 1
+        if not pending:
+            time.sleep(max(0.0, min(0.002, reqs[nxt]["at"] - now)))
+            continue
+        stats = srv.pump()
+        for i in list(pending):
+            s = srv.poll(ids[i])
+            if s["state"] in (dbnet.DBSRV_DONE, dbnet.DBSRV_FAILED):
+                st[i] = s
+                pending.discard(i)
+                srv.release(ids[i])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    s_end = srv.stats()
+    events = s_end["events"] - ev0
+    launches = 2 * s_end["iterations"]
+
+    # capacity: the first --separate-requests requests submitted at once
+    n_sep = min(args.separate_requests, len(reqs))
+    e1 = srv.stats()["events"]
+    t1 = time.perf_counter()
+    sat = []
+    for r in reqs[:n_sep]:
+        g, p, _ = cat[r["cat"]]
+        sat.append(srv.submit(g, p, r["n_steps"], seed=r["seed"], net_id=r["net_id"]))
+    srv.drain()
+    torch.cuda.synchronize()
+    sat_wall = time.perf_counter() - t1
+    sat_events = srv.stats()["events"] - e1
+    srv.close()
+    failed = sum(1 for s in st if s["state"] != dbnet.DBSRV_DONE)
+    lat = np.array([s["latency_s"] / r["bio_s"] for s, r in zip(st, reqs)])
+    q = np.array([s["queued_s"] for s in st])
+    value = events / wall
+
+    # one network per launch: the same first requests, each created,
+    # stepped and read alone; their service times then replayed through a
+    # FIFO queue with the same arrival times
+    service = []
+    sep_events = 0
+    for r in reqs[:n_sep]:
+        g, p, _ = cat[r["cat"]]
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        net = dbnet.Network(g, p, dict(seed=r["seed"], net_id=r["net_id"]), stream)
+        net.step(r["n_steps"])
+        sep_events += net.stats()["events"]
+        net.bold()
+        net.close()
+        service.append(time.perf_counter() - a)
+    end = 0.0
+    sep_lat = []
+    for r, sv in zip(reqs[:n_sep], service):
+        end = max(end, r["at"]) + sv
+        sep_lat.append((end - r["at"]) / r["bio_s"])
+    sep_lat = np.array(sep_lat)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(reqs),
+        "warmup": 0, "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators, f64 BOLD",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": "serving: %d requests, Poisson arrivals at %.1f/s, networks of "
+                               "1e4-1e6 neurons (log-uniform), in-degree 100-1000, 1-50 regions, "
+                               "0.5-5 s biological, ~10 Hz; %d catalogue networks, each request "
+                               "uploads its own copy" % (len(reqs), args.arrival_hz, args.catalogue),
+                   "step": "one request", "l2": "not flushed: resident edges exceed L2"},
+        "latency_per_bio_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "mean": float(lat.mean())},
+        "queue_s": {"p50": float(np.percentile(q, 50)), "p99": float(np.percentile(q, 99))},
+        "failed": failed, "wall_s": wall, "generate_s": t_gen,
+        "separate": {"value": sep_events / sum(service), "unit": UNIT, "requests": n_sep,
+                     "latency_per_bio_s": {"p50": float(np.percentile(sep_lat, 50)),
+                                           "p99": float(np.percentile(sep_lat, 99))},
+                     "what": "the first %d requests, each as its own network (create, step, read, "
+                             "destroy) one after another; latency from their measured service "
+                             "times in a FIFO queue with the same arrivals" % n_sep},
+        "saturated": {"value": sat_events / sat_wall, "unit": UNIT, "requests": n_sep,
+                      "what": "the same first %d requests submitted at once and drained "
+                              "(capacity of the served form)" % n_sep},
+        "served_over_separate": (sat_events / sat_wall) / (sep_events / sum(service)),
+        "clocks": clk, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
 
 
 # -------------------------------------------------------- reference arm ----
