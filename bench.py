@@ -48,6 +48,10 @@ UNIT = "events/s"
 
 
 def parse():
+    return parse_from(None)
+
+
+def parse_from(argv):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -70,7 +74,7 @@ def parse():
     ap.add_argument("--catalogue", type=int, default=16,
                     help="distinct request networks built before the stream starts")
     ap.add_argument("--separate-requests", type=int, default=40)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_config(args, rank_count):
@@ -136,6 +140,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers ----
+def rank_seed(rank):
+    """Graph seed of replica `rank` (each rank simulates its own network)."""
+    import synth
+    return synth.seed_for(1) + 1000 * rank
+
+
+def combine_ranks(events, spikes, neurons, dev_ms, world, device):
+    """Whole-job totals over the replicas: events, spikes and neurons summed,
+    device time the maximum over ranks (the slowest replica bounds the job)."""
+    import torch
+    import torch.distributed as dist
+    tot = torch.tensor([events, spikes, neurons], dtype=torch.float64, device=device)
+    mx = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    e, s, n = (float(x) for x in tot.tolist())
+    return e, s, n, float(mx.item())
+
+
 def kernels_sha():
     p = os.path.join(ROOT, "paper_2211_15963_gb300", "csrc", "kernels.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -224,7 +248,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)  # the library and every event use this stream
 
     alloc, keep = pinned_alloc(torch)
-    seed = synth.seed_for(1) + 1000 * rank
+    seed = rank_seed(rank)
     t_gen = time.perf_counter()
     g = synth.make_graph([20000] * args.regions, args.k_in, seed, k_within=int(round(0.8 * args.k_in)),
                          d_within=(1, 50), d_cross=(50, 200), alloc=alloc)
@@ -261,13 +285,8 @@ def run_ours(args):
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     events = s1["events"] - s0["events"]
     spikes = s1["spikes"] - s0["spikes"]
-    tot = torch.tensor([events, spikes, g.n_neurons], dtype=torch.float64, device=dev)
-    mx = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-    events_all, spikes_all, neurons_all = (float(x) for x in tot.tolist())
-    ms_all = float(mx.item())
+    events_all, spikes_all, neurons_all, ms_all = combine_ranks(
+        events, spikes, g.n_neurons, dev_ms, world, dev)
     ms_per_step = ms_all / args.steps
     value = events_all / (ms_all * 1e-3)
 

@@ -1,0 +1,67 @@
+"""Host logic of bench.py that needs no GPU: the replica combination over
+ranks (run here as two gloo processes on the CPU), per-rank seeds, the
+reference arm's rank rule and the serving drive interpolation."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    per_rank = [(1000.0, 10.0, 2e6, 640.0), (3000.0, 30.0, 2e6, 655.5)][rank]
+    res = bench.combine_ranks(*per_rank, world, "cpu")
+    with open(os.path.join(out_dir, "r%d.json" % rank), "w") as f:
+        json.dump(res, f)
+    dist.destroy_process_group()
+
+
+def test_combine_ranks_over_two_gloo_processes(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        e, s, n, ms = json.load(open(tmp_path / ("r%d.json" % r)))
+        assert (e, s, n) == (4000.0, 40.0, 4e6)   # summed over the replicas
+        assert ms == 655.5                         # the slowest replica
+
+
+def test_single_rank_combination_is_identity():
+    import bench
+    assert bench.combine_ranks(7.0, 3.0, 5.0, 2.5, 1, "cpu") == (7.0, 3.0, 5.0, 2.5)
+
+
+def test_rank_seeds_differ():
+    import bench
+    seeds = [bench.rank_seed(r) for r in range(8)]
+    assert len(set(seeds)) == 8 and seeds[0] == 15973
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.run_reference(bench.parse_from([]))
+    assert capsys.readouterr().out == ""
+
+
+def test_serving_drive_interpolation():
+    import bench
+    for k, v in bench.SERVE_DRIVE:
+        assert abs(bench.serve_drive(k) - v) < 1e-12
+    assert bench.SERVE_DRIVE[0][1] < bench.serve_drive(200) < bench.SERVE_DRIVE[1][1]
+    assert bench.serve_drive(50) == bench.SERVE_DRIVE[0][1]
