@@ -166,16 +166,22 @@ def kernels_sha():
 
 
 def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, when
-    it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "traffic_mid_network.json")
+    """DRAM bytes per launch of `kernel` (ncu dram__bytes_read.sum +
+    dram__bytes_write.sum) from the committed summary
+    profiles/traffic_mid_network.md, when it was taken on the current kernel
+    source: its line `kernels.cu sha256[:16]: <sha>` must match, and its
+    table rows read `| <kernel> | <bytes per launch> | ...`."""
+    import re
+    p = os.path.join(ROOT, "profiles", "traffic_mid_network.md")
     try:
-        d = json.load(open(p))
-    except (OSError, ValueError):
+        txt = open(p).read()
+    except OSError:
         return None
-    if d.get("kernels_sha") != kernels_sha():
+    m = re.search(r"kernels\.cu sha256\[:16\]: ([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernels_sha():
         return None
-    return d.get("bytes_per_launch", {}).get(kernel)
+    m = re.search(r"^\| %s \| ([0-9]+) \|" % re.escape(kernel), txt, flags=re.M)
+    return int(m.group(1)) if m else None
 
 
 def peaks():
