@@ -276,7 +276,8 @@ void ens_destroy(dbens_t* h);
  * flight) and advances n_steps exactly as dbnet_step does.
  * Outputs (DEVICE arrays owned by the caller): V[n_pad], J[4][n_pad]
  * (channel-major, row stride n_pad), ref[n_pad] (u8), with n_pad = N rounded
- * up to a multiple of 1024; raster_step/raster_id[raster_cap] receive the
+ * up to a multiple of 1024, each 16-byte aligned (else DBNET_EINVAL: whole
+ * tiles move by bulk copies); raster_step/raster_id[raster_cap] receive the
  * spikes (unordered within a step; more than raster_cap are dropped and
  * counted).  *n_spikes and *n_events (host) receive the totals.
  * Limits: N <= DBNET_NOALLOC_MAX_NEURONS, R <= DBNET_NOALLOC_MAX_REGIONS and

@@ -45,12 +45,18 @@ constexpr int kDelThreads = 256;
 constexpr int kMaxThr = 16;         // Poisson inversion thresholds
 constexpr int kTileRegions = 8;     // region constants staged in shared memory
 
-struct RegionConst {
-  float dtC, gL, VL, Vth, Vreset, Iext;
-  float g[4], Vu[4], dec[4];
-  int32_t n_ref, q_ext, n_thr, exc_end;  // exc_end: first inhibitory local index
-  int32_t start, end, pad0, pad1;        // local neuron range [start, end)
-  uint32_t thr[kMaxThr];
+// 16-byte multiples: the update kernel moves these with bulk copies
+// (laid out as 16-byte vectors: the update kernel reads them with 128-bit loads)
+struct alignas(16) RegionConst {
+  float g[4];                        // channel conductance scales
+  float Vu[4];                       // reversal potentials
+  float dec[4];                      // per-step trace decay exp(-dt/tau_u)
+  float dtC, gL, VL, Vth;
+  float Vreset, Iext;
+  int32_t n_ref, q_ext;
+  int32_t n_thr, exc_end, start, end;  // exc_end: first inhibitory local index;
+                                       // local neuron range [start, end)
+  uint32_t thr[kMaxThr];             // Poisson inversion thresholds, non-decreasing
 };
 
 enum : int32_t {
@@ -59,7 +65,7 @@ enum : int32_t {
   kSeg32 = 2,
 };
 
-struct InstDesc {
+struct alignas(16) InstDesc {
   const int64_t* row_ptr;
   const uint16_t* rec;           // interleaved records, or nullptr for col/w/delay
   const uint32_t* col;
@@ -105,6 +111,7 @@ struct StepRef {
 enum : unsigned {
   kFlagHistOverflow = 1u,
   kFlagBoldOverflow = 2u,
+  kFlagWaitTimeout = 4u,  // a bounded device wait gave up (bulk copy not arrived)
 };
 
 struct EngineDev {

@@ -156,11 +156,13 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   // state loads first: they depend only on the tile, and the arrays cover
   // every padded tile
   const int64_t gi0 = (int64_t)tile * kTile + threadIdx.x * 4;
-  const float4 V4 = *reinterpret_cast<const float4*>(e.V + gi0);
+  // (state is streamed once per step: evict-first, so that the delivery's
+  // working set keeps the L2)
+  const float4 V4 = __ldcs(reinterpret_cast<const float4*>(e.V + gi0));
   float4 J4[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) J4[u] = *reinterpret_cast<const float4*>(e.J + u * e.stride + gi0);
-  const uchar4 rf = *reinterpret_cast<const uchar4*>(e.ref + gi0);
+  for (int u = 0; u < 4; ++u) J4[u] = __ldcs(reinterpret_cast<const float4*>(e.J + u * e.stride + gi0));
+  const uchar4 rf = __ldcs(reinterpret_cast<const uchar4*>(e.ref + gi0));
   const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
   const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
 
@@ -208,52 +210,60 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
       while (li >= rcp[r].end) ++r;
       reg[k] = r0 + r;
       const RegionConst& p = rcp[r];
+      const float4 G = *reinterpret_cast<const float4*>(p.g);
+      const float4 VU = *reinterpret_cast<const float4*>(p.Vu);
+      const float4 DE = *reinterpret_cast<const float4*>(p.dec);
+      const float4 M = *reinterpret_cast<const float4*>(&p.dtC);     // dtC gL VL Vth
+      const float4 Q = *reinterpret_cast<const float4*>(&p.Vreset);  // Vreset Iext n_ref q_ext
+      const int4 W = *reinterpret_cast<const int4*>(&p.n_thr);       // n_thr exc_end start end
       // background: Poisson count by integer inversion of 32 Philox bits
+      // (the thresholds are non-decreasing: count them up to the first miss)
       const uint32_t uu = (uint32_t)(x[k] >> 32);
       int c = 0;
-      for (int t = 0; t < p.n_thr; ++t) c += (uu >= p.thr[t]) ? 1 : 0;
-      const int ae = aE[k] + c * p.q_ext;
+      while (c < W.x && uu >= p.thr[c]) ++c;
+      const int ae = aE[k] + c * __float_as_int(Q.w);
       // membrane with the old V and traces
       const float vk = v[k];
+      const float gu[4] = {G.x, G.y, G.z, G.w}, vu[4] = {VU.x, VU.y, VU.z, VU.w};
       float Isyn = 0.0f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float gj = __fmul_rn(p.g[u], j[u][k]);
-        const float dv = __fsub_rn(p.Vu[u], vk);
+        const float gj = __fmul_rn(gu[u], j[u][k]);
+        const float dv = __fsub_rn(vu[u], vk);
         Isyn = __fadd_rn(Isyn, __fmul_rn(gj, dv));
       }
-      const float leak = __fmul_rn(p.gL, __fsub_rn(vk, p.VL));
+      const float leak = __fmul_rn(M.y, __fsub_rn(vk, M.z));
       float I = __fsub_rn(Isyn, leak);
-      I = __fadd_rn(I, p.Iext);
-      const float vn = __fadd_rn(vk, __fmul_rn(I, p.dtC));
+      I = __fadd_rn(I, Q.y);
+      const float vn = __fadd_rn(vk, __fmul_rn(I, M.x));
       // traces: decay, then this step's arrivals
       const float xE = __fmul_rn(__int2float_rn(ae), d.inv_two_S);
       const float xI = __fmul_rn(__int2float_rn(aI[k]), d.inv_two_S);
-      j[0][k] = __fadd_rn(__fmul_rn(p.dec[0], j[0][k]), xE);
-      j[1][k] = __fadd_rn(__fmul_rn(p.dec[1], j[1][k]), xE);
-      j[2][k] = __fadd_rn(__fmul_rn(p.dec[2], j[2][k]), xI);
-      j[3][k] = __fadd_rn(__fmul_rn(p.dec[3], j[3][k]), xI);
+      j[0][k] = __fadd_rn(__fmul_rn(DE.x, j[0][k]), xE);
+      j[1][k] = __fadd_rn(__fmul_rn(DE.y, j[1][k]), xE);
+      j[2][k] = __fadd_rn(__fmul_rn(DE.z, j[2][k]), xI);
+      j[3][k] = __fadd_rn(__fmul_rn(DE.w, j[3][k]), xI);
       // refractory clamp, threshold, reset
       if (rr[k] > 0) {
-        v[k] = p.Vreset;
+        v[k] = Q.x;
         rr[k] -= 1;
-      } else if (vn >= p.Vth) {
-        v[k] = p.Vreset;
-        rr[k] = p.n_ref;
+      } else if (vn >= M.w) {
+        v[k] = Q.x;
+        rr[k] = __float_as_int(Q.z);
         spk |= 1u << k;
-        if (li >= p.exc_end) cls_bits |= 1u << k;
+        if (li >= W.y) cls_bits |= 1u << k;
       } else {
         v[k] = vn;
       }
     }
-    *reinterpret_cast<float4*>(e.V + gi0) = make_float4(v[0], v[1], v[2], v[3]);
+    __stcs(reinterpret_cast<float4*>(e.V + gi0), make_float4(v[0], v[1], v[2], v[3]));
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      *reinterpret_cast<float4*>(e.J + u * e.stride + gi0) =
-          make_float4(j[u][0], j[u][1], j[u][2], j[u][3]);
-    *reinterpret_cast<uchar4*>(e.ref + gi0) =
-        make_uchar4((unsigned char)rr[0], (unsigned char)rr[1], (unsigned char)rr[2],
-                    (unsigned char)rr[3]);
+      __stcs(reinterpret_cast<float4*>(e.J + u * e.stride + gi0),
+             make_float4(j[u][0], j[u][1], j[u][2], j[u][3]));
+    __stcs(reinterpret_cast<uchar4*>(e.ref + gi0),
+           make_uchar4((unsigned char)rr[0], (unsigned char)rr[1], (unsigned char)rr[2],
+                       (unsigned char)rr[3]));
   }
 
   // ---- spikes: one ring append, spike and raster count per block ---------

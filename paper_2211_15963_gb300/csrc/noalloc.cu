@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstdint>
 
 #include <algorithm>
 #include <cmath>
@@ -160,6 +161,10 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
       raise(DBNET_EINVAL, "NULL argument");
     if (n_steps < 0 || raster_cap < 0 || (raster_cap > 0 && (!raster_step || !raster_id)))
       raise(DBNET_EINVAL, "bad step count or raster buffers");
+    // the update kernel moves whole tiles of V, J and ref with 16-byte bulk copies
+    if ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(J) |
+         reinterpret_cast<uintptr_t>(ref)) & 15u)
+      raise(DBNET_EINVAL, "V, J and ref must be 16-byte aligned");
     const int32_t N = graph->n_neurons, R = graph->n_regions;
     if (N < 1 || R < 1 || !graph->region_offsets || !graph->n_exc || !graph->row_ptr ||
         !graph->col || !graph->weight_bf16 || !graph->delay)
@@ -327,6 +332,7 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     CK(cudaMemcpyAsync(&ev, at(kOffEvents), sizeof(ev), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&flags, at(kOffFlags), sizeof(flags), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (flags & kFlagWaitTimeout) raise(DBNET_ETIMEOUT, "a bounded device wait gave up");
     if (flags & kFlagHistOverflow) raise(DBNET_ERANGE, "spike ring overflowed");
     *n_spikes = (int64_t)out_dyn.spikes;
     *n_events = (int64_t)ev;
