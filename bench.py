@@ -63,7 +63,7 @@ def parse_from(argv):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--regions", type=int, default=100, help="regions of 20,000 neurons")
     ap.add_argument("--k-in", type=int, default=1000, help="in-degree (80 %% within region)")
-    ap.add_argument("--workload", default="mid", choices=["mid", "ensemble", "serving"],
+    ap.add_argument("--workload", default="mid", choices=["mid", "ensemble", "serving", "nest"],
                     help="mid: the headline line; ensemble: 64-member HMDA ensemble (steps = "
                          "TRs) against one network per launch; serving: request stream")
     ap.add_argument("--members", type=int, default=64)
@@ -682,6 +682,79 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------- NEST-comparison workload ----
+# Supplementary Section 5 / Table 4: networks of 2-10 M neurons, in-degree
+# ~100, Euler step 1 ms, mean rates ~4.1 and ~12.1 Hz, 3 s simulated and the
+# last second timed.  The paper's model has no synaptic delay beyond Eq. 3's
+# one step, so every edge here has delay 1.  With dt = 1 ms the conductances
+# tuned for 0.1 ms make the explicit step stiff, so they are scaled by 0.2 and
+# the drive set for the two rates (a sweep on a 200,000-neuron network:
+# 4.13 and 12.08 Hz).
+NEST_SIZES_M = (2, 3, 4, 5, 10)
+NEST_G_SCALE = 0.2
+NEST_DRIVE = {4.1: 0.55, 12.1: 0.9}
+# Supplementary Table 4, one GPU, single precision: RTF at 2/3/4/5/10 M
+NEST_PAPER_RTF = {4.1: (4.49, 6.02, 7.49, 9.18, 17.79), 12.1: (7.99, 6.28, 7.82, 17.05, 24.32)}
+
+
+def run_nest(args):
+    import torch
+    import synth
+    import __graft_entry__
+    from paper_2211_15963_gb300 import dbnet
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    table = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    for i, n_m in enumerate(NEST_SIZES_M):
+        g = synth.make_graph([20000] * (50 * n_m), 100, synth.seed_for(5) + i, d_within=(1, 1),
+                             d_cross=(1, 1))
+        for rate, drive in NEST_DRIVE.items():
+            p = synth.default_region_params(I_ext=drive)
+            p["g_u"] = tuple(x * NEST_G_SCALE for x in p["g_u"])
+            net = dbnet.Network(g, p, dict(dt_ms=1.0, bin_ms=1.0, seed=synth.seed_for(5) + 100 + i),
+                                stream)
+            net.step(2000)
+            net.sync()
+            s0 = net.stats()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.step(1000)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            s1 = net.stats()
+            net.close()
+            table.append({"neurons": g.n_neurons, "target_hz": rate,
+                          "rate_hz": (s1["spikes"] - s0["spikes"]) / g.n_neurons,
+                          "rtf": ms / 1e3,
+                          "events_per_s": (s1["events"] - s0["events"]) / (ms * 1e-3),
+                          "paper_rtf_one_gpu": NEST_PAPER_RTF[rate][i]})
+        del g
+    clk = clocks.stop()
+    big = [t for t in table if t["neurons"] == 10_000_000 and t["target_hz"] == 12.1][0]
+    line = {
+        "metric": "real-time factor", "value": big["rtf"], "unit": "s per biological s",
+        "n_gpus": 1, "steps": 1, "warmup": 2, "ms_per_step": big["rtf"] * 1e3,
+        "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": "NEST-comparison networks: 2/3/4/5/10 M neurons, regions of "
+                               "20,000, in-degree 100, delay 1 step, dt 1 ms, ~4.1 and ~12.1 Hz; "
+                               "3 s simulated, the last second timed; value = 10 M at 12.1 Hz",
+                   "step": "the timed biological second"},
+        "table": table, "clocks": clk, "gpu_launches": 2 * 1000 * len(table),
+        "paper_context": "Supplementary Table 4: one GPU with 16 GB HBM2 (10.8 TFLOPS), "
+                         "their own connectome-derived networks",
+    }
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------- reference arm ----
 def run_reference(args):
     """The CPU oracle, as it stands, on the host cores: each step is a 10 ms
@@ -732,6 +805,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "nest":
+        run_nest(args)
     else:
         run_ours(args)
 

@@ -277,3 +277,21 @@ def test_autotuned_grid_gives_identical_results():
     assert np.array_equal(tuned.bold(), plain.bold())
     tuned.close()
     plain.close()
+
+
+def test_one_millisecond_step_without_delays():
+    """The paper's own setting (Euler step 1 ms, Eq. 3's one-step latency as
+    the only delay, Supplementary Sec. 5): matched-FP32 bit-exact over 1 s."""
+    g = synth.make_graph([6000, 4000], 100, 55, d_within=(1, 1), d_cross=(1, 1))
+    p = synth.default_region_params(I_ext=0.9)
+    p["g_u"] = tuple(x * 0.2 for x in p["g_u"])
+    net = _net(g, p, seed=3, dt_ms=1.0, bin_ms=1.0, tr_ms=100.0)
+    o = oracle.Sim(g, p, seed=3, dt_ms=1.0, bin_ms=1.0, tr_ms=100.0, precision=32)
+    net.step(1000)
+    o.step(1000)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 10_000
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "dt 1 ms")
+    assert np.allclose(net.bold(), o.bold(), rtol=1e-10, atol=1e-15)
