@@ -62,7 +62,8 @@ class OgRegion(ctypes.Structure):
                 ("Vu", ctypes.c_double * 4), ("tau_u", ctypes.c_double * 4),
                 ("g_u", ctypes.c_double * 4), ("I_ext", ctypes.c_double),
                 ("drive_rate_hz", ctypes.c_double), ("drive_K", ctypes.c_double),
-                ("w_ext", ctypes.c_double)]
+                ("w_ext", ctypes.c_double), ("ou_mu", ctypes.c_double),
+                ("ou_sigma", ctypes.c_double), ("ou_tau", ctypes.c_double)]
 
 
 class OgOptions(ctypes.Structure):
@@ -90,6 +91,10 @@ def lib():
             L.og_deliver_only.argtypes = [vp, vp, i64, i64]
             L.og_read_state.argtypes = [vp, vp, vp, vp]
             L.og_set_state.argtypes = [vp, vp, vp, vp]
+            L.og_read_ibg.argtypes = [vp, vp]
+            L.og_set_ibg.argtypes = [vp, vp]
+            L.og_box_muller.restype = d
+            L.og_box_muller.argtypes = [ctypes.c_uint64]
             L.og_info.argtypes = [vp, vp]
             for f in (L.og_read_raster,):
                 f.argtypes = [vp, vp, vp]
@@ -142,7 +147,15 @@ def region_struct(p: dict) -> OgRegion:
         arr = getattr(r, k)
         for u in range(4):
             arr[u] = float(p[k][u])
+    r.ou_mu = float(p.get("ou_mu", 0.0))
+    r.ou_sigma = float(p.get("ou_sigma", 0.0))
+    r.ou_tau = float(p.get("ou_tau", 10.0))
     return r
+
+
+def box_muller(word: int) -> float:
+    """The oracle's standard normal from one 64-bit Philox word."""
+    return lib().og_box_muller(int(word))
 
 
 class Sim:
@@ -196,6 +209,16 @@ class Sim:
         ref = np.zeros(self.N, dtype=np.int32)
         lib().og_read_state(self._h, V.ctypes.data, J.ctypes.data, ref.ctypes.data)
         return V, J, ref
+
+    def ibg(self) -> np.ndarray:
+        """The background OU current of every neuron."""
+        I = np.zeros(self.N)
+        lib().og_read_ibg(self._h, I.ctypes.data)
+        return I
+
+    def set_ibg(self, I) -> None:
+        a = np.ascontiguousarray(I, dtype=np.float64)
+        lib().og_set_ibg(self._h, a.ctypes.data)
 
     def set_state(self, V=None, J=None, ref=None) -> None:
         def p(a, dt):

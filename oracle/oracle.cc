@@ -35,6 +35,17 @@
 //     inversion of one 32-bit Philox word against FP64 Poisson CDF thresholds.
 //   * z (neural activity) = z_scale * spikes of the region in the last bin /
 //     region size; BW constants are inputs.
+//   * Optional background current I_bg (Eq. 1; Extended Data Table 2, "OU
+//     current"): Eq. 4 prints the noise as sqrt(2 tau) sigma eps with no
+//     step; the Euler-Maruyama form of Eq. 1 is used instead,
+//     I_bg += (mu - I_bg) dt/tau + sigma sqrt(2 dt/tau) xi, whose stationary
+//     standard deviation is sigma.  V is advanced with the old I_bg (added
+//     after I_ext, inside the dt/C bracket), then I_bg.  I_bg starts at mu.
+//     xi is a standard normal by the Box-Muller transform of the neuron's
+//     Philox word of stream 4: u1 = (high 32 bits + 1) 2^-32, u2 = low 32
+//     bits 2^-32, xi = sqrt(-2 ln u1) cos(2 pi u2), in FP64 (host and device
+//     log/cos differ, so with sigma > 0 only the FP64 results are meant to
+//     be compared, statistically).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -101,6 +112,7 @@ struct OgRegion {  // units: mV, ms, nF, uS, nA
   double C, gL, VL, Vth, Vreset, Tref;
   double Vu[4], tau_u[4], g_u[4];
   double I_ext, drive_rate_hz, drive_K, w_ext;
+  double ou_mu, ou_sigma, ou_tau;  // background OU current; off when mu = sigma = 0
 };
 
 struct OgOptions {
@@ -165,7 +177,16 @@ struct RegionConst {
   Real g[4], Vu[4], dec[4];
   int32_t n_ref, q_ext, n_thr;
   uint32_t thr[16];
+  int32_t ou_on;
+  Real ou_mu, ou_k, ou_s;  // mu, dt/tau, sigma sqrt(2 dt/tau)
 };
+
+// Standard normal from one 64-bit Philox word (Box-Muller, FP64).
+double box_muller(uint64_t w) {
+  const double u1 = ((double)(w >> 32) + 1.0) * std::ldexp(1.0, -32);  // (0, 1]
+  const double u2 = (double)(w & 0xFFFFFFFFull) * std::ldexp(1.0, -32);  // [0, 1)
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * 3.14159265358979323846 * u2);
+}
 
 struct SimBase {
   virtual ~SimBase() {}
@@ -173,6 +194,8 @@ struct SimBase {
   virtual void deliver_only(const int32_t* ids, int64_t count, int64_t n) = 0;
   virtual void read_state(double* V, double* J, int32_t* ref) const = 0;
   virtual void set_state(const double* V, const double* J, const int32_t* ref) = 0;
+  virtual void read_ibg(double* I) const = 0;
+  virtual void set_ibg(const double* I) = 0;
   // shared bookkeeping
   int32_t N = 0, R = 0, D = 0, S = 0, spb = 0, bins_per_tr = 0;
   int64_t n = 0, events = 0, spikes = 0, bins_done = 0;
@@ -191,6 +214,7 @@ struct Sim : SimBase {
   std::vector<int32_t> n_exc_end;  // absolute index where the inhibitory block starts
   std::vector<Real> V, J;  // J as [4][N]
   std::vector<int32_t> ref;
+  std::vector<Real> Ibg;   // background OU current
 
   int32_t class_of(int32_t i) const {
     int32_t r = region_of[(size_t)i];
@@ -241,8 +265,19 @@ struct Sim : SimBase {
         Real leak = p.gL * (v - p.VL);
         Real I = Isyn - leak;
         I = I + p.Iext;
+        if (p.ou_on) I = I + Ibg[(size_t)i];
         Real dV = I * p.dtC;
         Real vn = v + dV;
+        // background current (Eq. 1, Euler-Maruyama) after its use above
+        if (p.ou_on) {
+          Real& ib = Ibg[(size_t)i];
+          const Real xi = (Real)box_muller(neuron_word(o.seed, o.net_id, (uint64_t)n, i, 4));
+          Real dI = p.ou_mu - ib;
+          Real t1 = dI * p.ou_k;
+          ib = ib + t1;
+          Real t2 = p.ou_s * xi;
+          ib = ib + t2;
+        }
         // synaptic traces (Eq. 3): decay, then this step's arrivals
         Real xE = (Real)aE * inv2S;
         Real xI = (Real)aI * inv2S;
@@ -293,6 +328,13 @@ struct Sim : SimBase {
       if (refo) refo[i] = ref[(size_t)i];
       for (int u = 0; u < 4 && Jo; ++u) Jo[(size_t)u * N + i] = (double)J[(size_t)u * N + i];
     }
+  }
+
+  void read_ibg(double* I) const override {
+    for (int32_t i = 0; i < N; ++i) I[i] = (double)Ibg[(size_t)i];
+  }
+  void set_ibg(const double* I) override {
+    for (int32_t i = 0; i < N; ++i) Ibg[(size_t)i] = (Real)I[i];
   }
 
   void set_state(const double* Vi, const double* Ji, const int32_t* refi) override {
@@ -366,10 +408,17 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
     double lam = p.drive_K * p.drive_rate_hz * o->dt_ms * 1e-3;
     c.n_thr = og_poisson_thresholds(lam, c.thr);
     if (c.n_thr < 0) { *err = -1; delete s; return nullptr; }
+    c.ou_on = (p.ou_mu != 0.0 || p.ou_sigma != 0.0) ? 1 : 0;
+    if (c.ou_on && !(p.ou_tau > 0.0)) { *err = -1; delete s; return nullptr; }
+    c.ou_mu = (Real)p.ou_mu;
+    c.ou_k = c.ou_on ? (Real)(o->dt_ms / p.ou_tau) : (Real)0;
+    c.ou_s = c.ou_on ? (Real)(p.ou_sigma * std::sqrt(2.0 * o->dt_ms / p.ou_tau)) : (Real)0;
   }
   s->V.resize((size_t)N);
   s->J.assign((size_t)4 * N, (Real)0);
   s->ref.assign((size_t)N, 0);
+  s->Ibg.resize((size_t)N);
+  for (int32_t i = 0; i < N; ++i) s->Ibg[(size_t)i] = s->rc[(size_t)s->region_of[(size_t)i]].ou_mu;
   // initial V uniform in [V_reset, V_th) from the neuron's own Philox word
   for (int32_t i = 0; i < N; ++i) {
     const RegionConst<Real>& p = s->rc[(size_t)s->region_of[(size_t)i]];
@@ -416,6 +465,10 @@ void og_read_state(void* h, double* V, double* J, int32_t* ref) { ((SimBase*)h)-
 void og_set_state(void* h, const double* V, const double* J, const int32_t* ref) {
   ((SimBase*)h)->set_state(V, J, ref);
 }
+void og_read_ibg(void* h, double* I) { ((SimBase*)h)->read_ibg(I); }
+void og_set_ibg(void* h, const double* I) { ((SimBase*)h)->set_ibg(I); }
+// the Box-Muller normal the OU current draws from a Philox word
+double og_box_muller(uint64_t w) { return box_muller(w); }
 
 // info: [N, R, D, S, step, events, spikes, raster_len, bold_samples, bins_done]
 void og_info(void* h, int64_t* info) {

@@ -379,3 +379,70 @@ def test_matched_fp32_statistics_agree_with_fp64(small_graph):
     r32, r64 = res[32][0], res[64][0]
     assert abs(r32 - r64) / r64 < 0.03
     assert abs(res[32][1] - res[64][1]) < 0.05
+
+
+# ---------------------------------------------------- background OU current --
+def _empty_graph(N):
+    """N unconnected neurons in one region (all excitatory)."""
+    return synth.Graph(N, 1, np.array([0, N], np.int32), np.array([N], np.int32),
+                       np.zeros(N + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint16),
+                       np.zeros(0, np.uint8), 1)
+
+
+def test_box_muller_draws_are_standard_normal():
+    """The OU noise xi: Box-Muller of Philox words is N(0, 1) (KS test and
+    the first two moments)."""
+    stats = pytest.importorskip("scipy.stats")
+    words = np.concatenate([oracle.philox4x64([n, 7, 4, 0], [3, 9]) for n in range(12000)])
+    z = np.array([oracle.box_muller(int(w)) for w in words])
+    assert abs(z.mean()) < 5.0 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / len(z))
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+
+
+def test_ou_current_stationary_moments():
+    """Eq. 1 discretised (Euler-Maruyama) is the AR(1) process
+    I' = a I + (1 - a) mu + s xi with a = 1 - dt/tau, s = sigma sqrt(2 dt/tau):
+    stationary mean mu, variance s^2 / (1 - a^2) = sigma^2 / (1 - dt / (2 tau)),
+    lag-1 autocorrelation a (Extended Data Table 2 values)."""
+    N, dt, mu, sigma, tau = 20000, 0.1, 0.66, 0.12, 10.0
+    p = synth.default_region_params(ou_mu=mu, ou_sigma=sigma, ou_tau=tau, drive_rate_hz=0.0)
+    s = oracle.Sim(_empty_graph(N), p, precision=64)
+    s.step(1500)  # 15 time constants from I = mu
+    a_prev = s.ibg()
+    s.step(1)
+    a_now = s.ibg()
+    var_st = sigma ** 2 / (1.0 - dt / (2.0 * tau))
+    assert abs(a_now.mean() - mu) < 5.0 * math.sqrt(var_st / N)
+    assert abs(a_now.var() / var_st - 1.0) < 5.0 * math.sqrt(2.0 / N)
+    a = 1.0 - dt / tau
+    r = np.corrcoef(a_prev, a_now)[0, 1]
+    assert abs(r - a) < 5.0 * (1.0 - a * a) / math.sqrt(N)
+
+
+def test_ou_relaxation_without_noise_is_exact():
+    """sigma = 0: I_n = mu + (I_0 - mu) (1 - dt/tau)^n."""
+    N, mu, tau = 64, 0.5, 7.0
+    p = synth.default_region_params(ou_mu=mu, ou_sigma=0.0, ou_tau=tau, drive_rate_hz=0.0)
+    s = oracle.Sim(_empty_graph(N), p, precision=64)
+    I0 = np.linspace(-1.0, 2.0, N)
+    s.set_ibg(I0)
+    s.step(137)
+    expect = mu + (I0 - mu) * (1.0 - 0.1 / tau) ** 137
+    assert np.allclose(s.ibg(), expect, rtol=1e-12, atol=1e-14)
+
+
+def test_ou_current_enters_the_membrane_bracket_with_its_old_value():
+    """Eq. 5 (bracket times dt/C): one step from a chosen state with no
+    synaptic input gives V' = V + (dt/C)(-gL (V - VL) + I_ext + I_bg(t))."""
+    N = 8
+    p = synth.default_region_params(ou_mu=0.3, ou_sigma=0.0, ou_tau=5.0, drive_rate_hz=0.0,
+                                    Vth=100.0)
+    s = oracle.Sim(_empty_graph(N), p, precision=64)
+    V0 = np.linspace(-70.0, -52.0, N)
+    I0 = np.linspace(-0.4, 0.9, N)
+    s.set_state(V=V0, J=np.zeros((4, N)), ref=np.zeros(N, np.int32))
+    s.set_ibg(I0)
+    s.step(1)
+    expect = V0 + (0.1 / p["C"]) * (-p["gL"] * (V0 - p["VL"]) + p["I_ext"] + I0)
+    assert np.allclose(s.state()[0], expect, rtol=1e-13, atol=1e-12)
