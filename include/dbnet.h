@@ -88,11 +88,23 @@ typedef struct {
  *   drive_rate_hz, drive_K, w_ext  Poisson background: drive_K independent
  *                                  sources of rate drive_rate_hz per neuron,
  *                                  each event adding w_ext to the excitatory
- *                                  traces (Extended Data Table 2, "Input") */
+ *                                  traces (Extended Data Table 2, "Input")
+ *   ou_mu, ou_sigma, ou_tau        background current I_bg, an Ornstein-
+ *                                  Uhlenbeck process per neuron (Methods,
+ *                                  Eq. 1; Extended Data Table 2, "OU current":
+ *                                  0.66, 0.12, 10 ms), integrated by Euler-
+ *                                  Maruyama: I_bg += (mu - I_bg) dt/tau +
+ *                                  sigma sqrt(2 dt/tau) xi, xi standard normal
+ *                                  (Box-Muller of Philox stream 4, FP32 on the
+ *                                  device); added after I_ext inside the dt/C
+ *                                  bracket with its value before the step; it
+ *                                  starts at mu.  Off when ou_mu = ou_sigma = 0;
+ *                                  else ou_tau > 0 and ou_sigma >= 0. */
 typedef struct {
   double C, gL, VL, Vth, Vreset, Tref;
   double Vu[4], tau_u[4], g_u[4];
   double I_ext, drive_rate_hz, drive_K, w_ext;
+  double ou_mu, ou_sigma, ou_tau;
 } dbnet_region_params_t;
 
 /* Run options.
@@ -202,6 +214,11 @@ int dbnet_read_state(dbnet_t* h, float* V, float* J, int32_t* ref);
 /* Overwrite the neuron state (same layout; NULL leaves a field unchanged).
  * ref values must lie in 0..255. */
 int dbnet_set_state(dbnet_t* h, const float* V, const float* J, const int32_t* ref);
+
+/* Background OU current I_bg[N] (zero in regions without it): read, or
+ * overwrite before the next step. */
+int dbnet_read_ibg(dbnet_t* h, float* I_bg);
+int dbnet_set_ibg(dbnet_t* h, const float* I_bg);
 
 int dbnet_stats(dbnet_t* h, dbnet_stats_t* out);
 

@@ -147,7 +147,13 @@ void check_params(const dbnet_region_params_t& p, double dt) {
   if (!(p.drive_rate_hz >= 0) || !(p.drive_K >= 0) || !(p.w_ext >= 0) || !finite(p.w_ext) ||
       !finite(p.drive_rate_hz * p.drive_K))
     raise(DBNET_EINVAL, "drive constants must be finite and >= 0");
+  if (!finite(p.ou_mu) || !(p.ou_sigma >= 0) || !finite(p.ou_sigma))
+    raise(DBNET_EINVAL, "ou_mu must be finite and ou_sigma finite and >= 0");
+  if ((p.ou_mu != 0.0 || p.ou_sigma != 0.0) && !(p.ou_tau > 0 && finite(p.ou_tau)))
+    raise(DBNET_EINVAL, "ou_tau must be > 0 when the OU current is on");
 }
+
+static bool ou_on(const dbnet_region_params_t& p) { return p.ou_mu != 0.0 || p.ou_sigma != 0.0; }
 
 // Thresholds of the integer-inversion Poisson draw: floor(P(X <= k) 2^32) for
 // the leading k (at most 16) whose value stays below 2^32.
@@ -188,6 +194,12 @@ RegionConst region_const(const dbnet_region_params_t& p, double dt, int S, int32
   c.start = start;
   c.end = end;
   c.exc_end = exc_end;
+  if (ou_on(p)) {
+    c.ou_on = 1;
+    c.ou_mu = (float)p.ou_mu;
+    c.ou_k = (float)(dt / p.ou_tau);
+    c.ou_s = (float)(p.ou_sigma * std::sqrt(2.0 * dt / p.ou_tau));
+  }
   return c;
 }
 
@@ -240,7 +252,10 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     regions += sp.graph->R;
     dmax_all = std::max(dmax_all, sp.graph->max_delay);
   }
-  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream);
+  bool any_ou = false;
+  for (const auto& sp : specs)
+    for (const auto& p : sp.params) any_ou = any_ou || ou_on(p);
+  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream, any_ou);
   int64_t t = 0;
   int32_t r = 0;
   for (int k = 0; k < n; ++k) {
@@ -253,7 +268,7 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
 }
 
 void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
-                       const dbnet_options_t& common, void* user_stream) {
+                       const dbnet_options_t& common, void* user_stream, bool any_ou) {
   if (user_stream) {
     stream = (cudaStream_t)user_stream;
     own_stream = false;
@@ -273,8 +288,10 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
 
   V.alloc(stride);
   J.alloc(4 * stride);
+  Ibg.alloc(stride);
   ref.alloc(stride);
   acc.alloc(stride);
+  CK(cudaMemsetAsync(Ibg.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(V.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
   CK(cudaMemsetAsync(ref.p, 0, stride, stream));
@@ -332,6 +349,8 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev = EngineDev{};
   dev.V = V.p;
   dev.J = J.p;
+  dev.Ibg = Ibg.p;
+  dev.any_ou = any_ou ? 1 : 0;
   dev.ref = ref.p;
   dev.acc = acc.p;
   dev.stride = stride;
@@ -411,6 +430,8 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
   d.seg_kind = g.seg_kind;
   d.dmax = g.max_delay;
   d.seg_stride = g.seg_stride;
+  for (const auto& p : sp.params) d.ou = d.ou || ou_on(p);
+  if (d.ou && !dev.any_ou) raise(DBNET_EUNSUPPORTED, "this engine was built without the OU current");
   d.region_offsets = g.ro.p;
   d.rc = ih.rc.p;
   d.bold = ih.bold.p;
@@ -896,6 +917,28 @@ int dbnet_set_state(dbnet_t* h, const float* V, const float* J, const int32_t* r
         CK(cudaMemcpy(e.J.p + u * e.stride + base, J + (int64_t)u * N, sizeof(float) * N,
                       cudaMemcpyHostToDevice));
     if (ref) CK(cudaMemcpy(e.ref.p + base, r.data(), N, cudaMemcpyHostToDevice));
+  });
+}
+
+int dbnet_read_ibg(dbnet_t* h, float* I_bg) {
+  if (!h || !I_bg) return DBNET_EINVAL;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    e.sync();
+    const InstHost& ih = e.inst[h->inst];
+    CK(cudaMemcpy(I_bg, e.Ibg.p + (int64_t)ih.first_tile * kTile, sizeof(float) * ih.graph->N,
+                  cudaMemcpyDeviceToHost));
+  });
+}
+
+int dbnet_set_ibg(dbnet_t* h, const float* I_bg) {
+  if (!h || !h->own || !I_bg) return DBNET_EINVAL;
+  return guarded(h->eng, [&] {
+    Engine& e = *h->eng;
+    e.sync();
+    const InstHost& ih = e.inst[h->inst];
+    CK(cudaMemcpy(e.Ibg.p + (int64_t)ih.first_tile * kTile, I_bg, sizeof(float) * ih.graph->N,
+                  cudaMemcpyHostToDevice));
   });
 }
 

@@ -57,6 +57,8 @@ struct alignas(16) RegionConst {
   int32_t n_thr, exc_end, start, end;  // exc_end: first inhibitory local index;
                                        // local neuron range [start, end)
   uint32_t thr[kMaxThr];             // Poisson inversion thresholds, non-decreasing
+  float ou_mu, ou_k, ou_s;           // background OU current: mu, dt/tau,
+  int32_t ou_on;                     //   sigma sqrt(2 dt/tau); 1 when on
 };
 
 enum : int32_t {
@@ -87,7 +89,7 @@ struct alignas(16) InstDesc {
   uint32_t tmask;
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;
-  int32_t seg_kind, dmax, seg_stride, pad_s;
+  int32_t seg_kind, dmax, seg_stride, ou;  // ou: some region has the OU current
   double h_bw, z_scale, kappa, gamma, tau, alpha, rho, V0;
 };
 
@@ -117,6 +119,7 @@ enum : unsigned {
 struct EngineDev {
   float* V;
   float* J;
+  float* Ibg;            // background OU current per neuron
   uint8_t* ref;
   int2* acc;
   int64_t stride;
@@ -139,6 +142,7 @@ struct EngineDev {
   unsigned int* flags;
   int32_t D;
   int32_t n_inst, n_tiles, total_R;
+  int32_t any_ou;        // launch the update with the OU current
 };
 
 // Launchers (kernels.cu)

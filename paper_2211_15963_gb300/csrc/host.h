@@ -206,7 +206,7 @@ struct Engine {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<InstHost> inst;
-  DevBuf<float> V, J;
+  DevBuf<float> V, J, Ibg;
   DevBuf<uint8_t> ref;
   DevBuf<int2> acc;
   DevBuf<InstDesc> desc;
@@ -248,8 +248,9 @@ struct Engine {
   void init(const std::vector<InstSpec>& specs, void* user_stream);
   // Empty capacity for instances placed later: every tile and region slot
   // starts unused (the kernels skip it); D = longest delay + 1.
+  // any_ou: launch the update with the background OU current.
   void init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
-                 const dbnet_options_t& common, void* user_stream);
+                 const dbnet_options_t& common, void* user_stream, bool any_ou);
   // Put instance k on tiles [first_tile, +tiles of its graph) and region
   // slots [rbase, +R): its constants, buffers and initial state; its step 0
   // is the next iteration enqueued, and it stops after n_end steps.

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_init_state(EngineDev e, int ins
   const int64_t gi0 = (int64_t)(first_tile + blockIdx.x) * kTile + threadIdx.x * 4;
   const int32_t li0 = (int32_t)(gi0 - d.base);
   float v4[4] = {0.f, 0.f, 0.f, 0.f};
+  float b4[4] = {0.f, 0.f, 0.f, 0.f};  // background OU current starts at its mean
   unsigned long long c[4] = {0ull, (unsigned long long)(li0 >> 2), 1ull, 0ull};
   philox4x64_10(c, d.seed, d.net_id);
   int r = li0 < d.N ? find_region(d.region_offsets, d.R, li0) : 0;
@@ -98,9 +99,11 @@ __global__ void __launch_bounds__(kUpdThreads) k_init_state(EngineDev e, int ins
       const float u = __fmul_rn(__ull2float_rn(c[k] >> 40), 5.9604644775390625e-08f);  // 2^-24
       const float span = __fsub_rn(p.Vth, p.Vreset);
       v4[k] = __fadd_rn(p.Vreset, __fmul_rn(span, u));
+      if (p.ou_on) b4[k] = p.ou_mu;
     }
   }
   *reinterpret_cast<float4*>(e.V + gi0) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+  if (e.Ibg) *reinterpret_cast<float4*>(e.Ibg + gi0) = make_float4(b4[0], b4[1], b4[2], b4[3]);
 #pragma unroll
   for (int u = 0; u < 4; ++u)
     *reinterpret_cast<float4*>(e.J + u * e.stride + gi0) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -146,6 +149,16 @@ __global__ void k_close(EngineDev e, unsigned long long g) {
 
 __global__ void k_set_base(unsigned long long* base, unsigned long long g) { *base = g; }
 
+// Standard normal from one Philox word (Box-Muller): u1 = (high 32 bits + 1)
+// 2^-32 in (0, 1], u2 = low 32 bits 2^-32, sqrt(-2 ln u1) cos(2 pi u2) in FP32.
+__device__ __forceinline__ float normal_from_word(unsigned long long w) {
+  const float u1 = __double2float_rn(((double)(uint32_t)(w >> 32) + 1.0) * 2.3283064365386963e-10);
+  const float u2 = __double2float_rn((double)(uint32_t)w * 2.3283064365386963e-10);
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// OU: also integrate the background OU current (instances with d.ou).
+template <bool OU>
 __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef sr) {
   __shared__ RegionConst s_rc[kTileRegions];
   __shared__ uint32_t s_wtot[kUpdThreads / 32];
@@ -163,6 +176,8 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
 #pragma unroll
   for (int u = 0; u < 4; ++u) J4[u] = __ldcs(reinterpret_cast<const float4*>(e.J + u * e.stride + gi0));
   const uchar4 rf = __ldcs(reinterpret_cast<const uchar4*>(e.ref + gi0));
+  float4 B4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (OU) B4 = __ldcs(reinterpret_cast<const float4*>(e.Ibg + gi0));
   const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
   const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
 
@@ -193,6 +208,14 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     *reinterpret_cast<int4*>(e.acc + gi0 + 2) = make_int4(0, 0, 0, 0);
     unsigned long long x[4] = {(unsigned long long)n, (unsigned long long)(li0 >> 2), 0ull, 0ull};
     philox4x64_10(x, d.seed, d.net_id);
+    float ib[4] = {B4.x, B4.y, B4.z, B4.w};
+    unsigned long long xo[4] = {0ull, 0ull, 0ull, 0ull};
+    if (OU && d.ou) {  // the OU noise: stream 4
+      xo[0] = (unsigned long long)n;
+      xo[1] = (unsigned long long)(li0 >> 2);
+      xo[2] = 4ull;
+      philox4x64_10(xo, d.seed, d.net_id);
+    }
 
     float v[4] = {V4.x, V4.y, V4.z, V4.w};
     float j[4][4] = {{J4[0].x, J4[0].y, J4[0].z, J4[0].w},
@@ -235,7 +258,18 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
       const float leak = __fmul_rn(M.y, __fsub_rn(vk, M.z));
       float I = __fsub_rn(Isyn, leak);
       I = __fadd_rn(I, Q.y);
+      float4 OUc = make_float4(0.f, 0.f, 0.f, 0.f);  // mu, dt/tau, sigma sqrt(2 dt/tau), on
+      if (OU && d.ou) {
+        OUc = *reinterpret_cast<const float4*>(&p.ou_mu);
+        if (__float_as_int(OUc.w)) I = __fadd_rn(I, ib[k]);  // I_bg before this step
+      }
       const float vn = __fadd_rn(vk, __fmul_rn(I, M.x));
+      if (OU && d.ou && __float_as_int(OUc.w)) {  // Eq. 1, Euler-Maruyama
+        const float xi = normal_from_word(xo[k]);
+        const float t1 = __fmul_rn(__fsub_rn(OUc.x, ib[k]), OUc.y);
+        ib[k] = __fadd_rn(ib[k], t1);
+        ib[k] = __fadd_rn(ib[k], __fmul_rn(OUc.z, xi));
+      }
       // traces: decay, then this step's arrivals
       const float xE = __fmul_rn(__int2float_rn(ae), d.inv_two_S);
       const float xI = __fmul_rn(__int2float_rn(aI[k]), d.inv_two_S);
@@ -264,6 +298,7 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     __stcs(reinterpret_cast<uchar4*>(e.ref + gi0),
            make_uchar4((unsigned char)rr[0], (unsigned char)rr[1], (unsigned char)rr[2],
                        (unsigned char)rr[3]));
+    if (OU && d.ou) __stcs(reinterpret_cast<float4*>(e.Ibg + gi0), make_float4(ib[0], ib[1], ib[2], ib[3]));
   }
 
   // ---- spikes: one ring append, spike and raster count per block ---------
@@ -623,7 +658,8 @@ void launch_init_state(const EngineDev& e, int inst, int n_tiles_inst, int first
 }
 
 void launch_update(const EngineDev& e, StepRef sr, cudaStream_t s) {
-  k_update<<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+  if (e.any_ou) k_update<true><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+  else k_update<false><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
 }
 
 void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s) {

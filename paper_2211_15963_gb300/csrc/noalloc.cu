@@ -182,7 +182,11 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
       if (graph->n_exc[r] < 0 || graph->n_exc[r] > ro[r + 1] - ro[r]) raise(DBNET_EINVAL, "n_exc out of range");
     }
     check_options(*options);
-    for (int32_t r = 0; r < R; ++r) check_params(params[r], options->dt_ms);
+    for (int32_t r = 0; r < R; ++r) {
+      check_params(params[r], options->dt_ms);
+      if (params[r].ou_mu != 0.0 || params[r].ou_sigma != 0.0)
+        raise(DBNET_EUNSUPPORTED, "the allocation-free entry point has no background OU state");
+    }
 
     cudaStream_t s = (cudaStream_t)cuda_stream;
     unsigned char* base = scratch_on_current_device();

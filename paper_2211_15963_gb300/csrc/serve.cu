@@ -448,7 +448,8 @@ int dbsrv_create(const dbsrv_options_t* options, void* cuda_stream, dbsrv_t** ou
     if (tiles * kTile >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "max_neurons too large");
     s->opt = o;
     s->eng.reset(new Engine());
-    s->eng->init_pool(o.max_requests, tiles, o.max_regions, o.max_delay + 1, o.run, cuda_stream);
+    s->eng->init_pool(o.max_requests, tiles, o.max_regions, o.max_delay + 1, o.run, cuda_stream,
+                      true);  // any request may bring the OU current
     s->eng->set_extent(1, 1);
     s->arena.init(o.arena_bytes);
     CK(cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking));

@@ -46,7 +46,8 @@ class dbnet_graph_t(ctypes.Structure):
 class dbnet_region_params_t(ctypes.Structure):
     _fields_ = [("C", _d), ("gL", _d), ("VL", _d), ("Vth", _d), ("Vreset", _d), ("Tref", _d),
                 ("Vu", _d * 4), ("tau_u", _d * 4), ("g_u", _d * 4), ("I_ext", _d),
-                ("drive_rate_hz", _d), ("drive_K", _d), ("w_ext", _d)]
+                ("drive_rate_hz", _d), ("drive_K", _d), ("w_ext", _d),
+                ("ou_mu", _d), ("ou_sigma", _d), ("ou_tau", _d)]
 
 
 class dbnet_options_t(ctypes.Structure):
@@ -116,6 +117,8 @@ _SIGS = {
     "dbnet_read_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "dbnet_set_state": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "dbnet_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dbnet_stats_t)]),
+    "dbnet_read_ibg": (ctypes.c_int, [_vp, _vp]),
+    "dbnet_set_ibg": (ctypes.c_int, [_vp, _vp]),
     "dbnet_destroy": (None, [_vp]),
     "ens_create": (ctypes.c_int, [ctypes.POINTER(dbnet_graph_t), _vp, _i32, _vp,
                                   ctypes.POINTER(dbnet_options_t), ctypes.POINTER(dbens_enkf_t),
@@ -228,6 +231,9 @@ def region_params(p: dict) -> dbnet_region_params_t:
     r = dbnet_region_params_t()
     for k in ("C", "gL", "VL", "Vth", "Vreset", "Tref", "I_ext", "drive_rate_hz", "drive_K", "w_ext"):
         setattr(r, k, float(p[k]))
+    r.ou_mu = float(p.get("ou_mu", 0.0))
+    r.ou_sigma = float(p.get("ou_sigma", 0.0))
+    r.ou_tau = float(p.get("ou_tau", 10.0))
     for k in ("Vu", "tau_u", "g_u"):
         arr = getattr(r, k)
         for u in range(4):
@@ -334,6 +340,17 @@ def dbnet_set_state(h, V=None, J=None, ref=None) -> None:
     _check(lib().dbnet_set_state(h, _addr(Va), _addr(Ja), _addr(ra)), "dbnet_set_state")
 
 
+def dbnet_read_ibg(h, n_neurons: int) -> np.ndarray:
+    I = np.zeros(n_neurons, dtype=np.float32)
+    _check(lib().dbnet_read_ibg(h, I.ctypes.data), "dbnet_read_ibg")
+    return I
+
+
+def dbnet_set_ibg(h, I) -> None:
+    a = np.ascontiguousarray(I, dtype=np.float32)
+    _check(lib().dbnet_set_ibg(h, a.ctypes.data), "dbnet_set_ibg")
+
+
 def dbnet_destroy(h) -> None:
     if h:
         lib().dbnet_destroy(h)
@@ -373,6 +390,12 @@ class Network:
 
     def set_state(self, V=None, J=None, ref=None) -> None:
         dbnet_set_state(self.h, V, J, ref)
+
+    def ibg(self) -> np.ndarray:
+        return dbnet_read_ibg(self.h, self.N)
+
+    def set_ibg(self, I) -> None:
+        dbnet_set_ibg(self.h, I)
 
     def close(self) -> None:
         if getattr(self, "h", None):

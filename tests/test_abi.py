@@ -126,3 +126,10 @@ def test_server_host_validation(lib):
     o = dbnet.dbsrv_options_default()
     assert o.max_requests == 64 and o.max_delay == 255 and o.chunk_steps == 256
     assert o.run.dt_ms == 0.1 and o.run.autotune_at == 2000
+
+
+def test_ou_parameters_are_validated(lib):
+    g = _tiny_graph()
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(ou_mu=0.5, ou_tau=0.0))
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(ou_sigma=-0.1, ou_tau=5.0))
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(ou_mu=float("nan"), ou_tau=5.0))

@@ -295,3 +295,53 @@ def test_one_millisecond_step_without_delays():
     assert np.array_equal(st, rs) and np.array_equal(ids, rids)
     _assert_same_state(net, o, "dt 1 ms")
     assert np.allclose(net.bold(), o.bold(), rtol=1e-10, atol=1e-15)
+
+
+def test_ou_current_without_noise_bit_exact():
+    """Background OU current with sigma = 0 (Eq. 1 without the noise term):
+    deterministic relaxation of I_bg from a chosen start, inside the
+    membrane bracket -- matched-FP32 bit-exact, I_bg included.  One region
+    has the current, one does not."""
+    g = synth.make_graph([1800, 1300], 80, 61, d_within=(1, 25), d_cross=(25, 70))
+    p = [synth.default_region_params(I_ext=0.6, ou_mu=0.35, ou_sigma=0.0, ou_tau=8.0),
+         synth.default_region_params()]
+    net = _net(g, p, seed=12)
+    o = oracle.Sim(g, p, seed=12, precision=32)
+    I0 = np.random.default_rng(5).uniform(-0.5, 1.0, g.n_neurons).astype(np.float32)
+    net.set_ibg(I0)
+    o.set_ibg(I0.astype(np.float64))
+    net.step(800)
+    o.step(800)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 500
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "OU, sigma 0")
+    assert np.array_equal(net.ibg().astype(np.float64), o.ibg())
+
+
+def test_ou_current_noise_statistics():
+    """sigma > 0 (Extended Data Table 2: mu 0.66, sigma 0.12, tau 10 ms): the
+    device's I_bg has the AR(1) stationary mean and variance
+    sigma^2 / (1 - dt / (2 tau)), and the network's rate and ISI CV match the
+    FP64 oracle (host and device normals differ, so only statistically)."""
+    g = synth.small_network()
+    mu, sigma, tau, dt = 0.66, 0.12, 10.0, 0.1
+    p = synth.default_region_params(I_ext=0.25, ou_mu=mu, ou_sigma=sigma, ou_tau=tau)
+    T = 20000
+    net = _net(g, p, seed=77, raster_capacity=1 << 23)
+    net.step(T)
+    o = oracle.Sim(g, p, seed=77, precision=64)
+    o.step(T)
+    I = net.ibg().astype(np.float64)
+    N = g.n_neurons
+    var_st = sigma ** 2 / (1.0 - dt / (2.0 * tau))
+    assert abs(I.mean() - mu) < 5.0 * np.sqrt(var_st / N)
+    assert abs(I.var() / var_st - 1.0) < 5.0 * np.sqrt(2.0 / N)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    r_gpu = len(ids) / N / (T * 1e-4)
+    r_64 = len(rids) / N / (T * 1e-4)
+    assert r_64 > 1.0
+    assert abs(r_gpu - r_64) / r_64 < 0.03, (r_gpu, r_64)
+    assert abs(metrics.isi_cv(st, ids) - metrics.isi_cv(rs, rids)) < 0.03
