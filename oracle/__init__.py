@@ -63,7 +63,8 @@ class OgRegion(ctypes.Structure):
                 ("g_u", ctypes.c_double * 4), ("I_ext", ctypes.c_double),
                 ("drive_rate_hz", ctypes.c_double), ("drive_K", ctypes.c_double),
                 ("w_ext", ctypes.c_double), ("ou_mu", ctypes.c_double),
-                ("ou_sigma", ctypes.c_double), ("ou_tau", ctypes.c_double)]
+                ("ou_sigma", ctypes.c_double), ("ou_tau", ctypes.c_double),
+                ("iext_shape", ctypes.c_double)]
 
 
 class OgOptions(ctypes.Structure):
@@ -95,6 +96,8 @@ def lib():
             L.og_set_ibg.argtypes = [vp, vp]
             L.og_box_muller.restype = d
             L.og_box_muller.argtypes = [ctypes.c_uint64]
+            L.og_gamma_draw.restype = d
+            L.og_gamma_draw.argtypes = [d, ctypes.c_uint64, ctypes.c_uint64, i64]
             L.og_info.argtypes = [vp, vp]
             for f in (L.og_read_raster,):
                 f.argtypes = [vp, vp, vp]
@@ -150,7 +153,13 @@ def region_struct(p: dict) -> OgRegion:
     r.ou_mu = float(p.get("ou_mu", 0.0))
     r.ou_sigma = float(p.get("ou_sigma", 0.0))
     r.ou_tau = float(p.get("ou_tau", 10.0))
+    r.iext_shape = float(p.get("iext_shape", 0.0))
     return r
+
+
+def gamma_draw(k: float, seed: int, net_id: int, i: int) -> float:
+    """The oracle's Gamma(k, 1) draw for neuron i's injected-current factor."""
+    return lib().og_gamma_draw(float(k), int(seed), int(net_id), int(i))
 
 
 def box_muller(word: int) -> float:

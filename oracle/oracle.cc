@@ -46,6 +46,13 @@
 //     bits 2^-32, xi = sqrt(-2 ln u1) cos(2 pi u2), in FP64 (host and device
 //     log/cos differ, so with sigma > 0 only the FP64 results are meant to
 //     be compared, statistically).
+//   * Heterogeneous injected current (Methods: the I_ext,i are Gamma
+//     distributed with region hyperparameters): with a region shape k > 0,
+//     neuron i receives I_ext * G_i / k, G_i ~ Gamma(k, 1) drawn once by the
+//     Marsaglia-Tsang method (ACM TOMS 26(3), 2000) from its Philox words of
+//     stream 5 (attempt a uses counter (0, i, 5, a): word 0 a Box-Muller
+//     normal, word 1 the acceptance uniform, word 2 for k < 1 the uniform of
+//     G(k) = G(k + 1) U^(1/k)), in FP64, rounded once to the state type.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -113,6 +120,7 @@ struct OgRegion {  // units: mV, ms, nF, uS, nA
   double Vu[4], tau_u[4], g_u[4];
   double I_ext, drive_rate_hz, drive_K, w_ext;
   double ou_mu, ou_sigma, ou_tau;  // background OU current; off when mu = sigma = 0
+  double iext_shape;               // > 0: per-neuron I_ext factor G/k, G ~ Gamma(k, 1)
 };
 
 struct OgOptions {
@@ -179,13 +187,40 @@ struct RegionConst {
   uint32_t thr[16];
   int32_t ou_on;
   Real ou_mu, ou_k, ou_s;  // mu, dt/tau, sigma sqrt(2 dt/tau)
+  int32_t het;             // per-neuron I_ext factors
 };
+
+// A uniform in (0, 1] from the high half of a Philox word.
+double unit_open(uint64_t w) { return ((double)(w >> 32) + 1.0) * std::ldexp(1.0, -32); }
 
 // Standard normal from one 64-bit Philox word (Box-Muller, FP64).
 double box_muller(uint64_t w) {
   const double u1 = ((double)(w >> 32) + 1.0) * std::ldexp(1.0, -32);  // (0, 1]
   const double u2 = (double)(w & 0xFFFFFFFFull) * std::ldexp(1.0, -32);  // [0, 1)
   return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * 3.14159265358979323846 * u2);
+}
+
+// Gamma(k, 1) for neuron i from its stream-5 Philox words (Marsaglia-Tsang).
+double gamma_draw(double k, uint64_t seed, uint64_t net_id, int64_t i) {
+  const uint64_t key[2] = {seed, net_id};
+  const double kk = k < 1.0 ? k + 1.0 : k;
+  const double d = kk - 1.0 / 3.0;
+  const double c = 1.0 / std::sqrt(9.0 * d);
+  for (uint64_t a = 0;; ++a) {
+    const uint64_t ctr[4] = {0, (uint64_t)i, 5, a};
+    uint64_t w[4];
+    philox4x64_10(ctr, key, w);
+    const double x = box_muller(w[0]);
+    const double t = 1.0 + c * x;
+    if (t <= 0.0) continue;
+    const double v = t * t * t;
+    const double u = unit_open(w[1]);
+    if (std::log(u) < 0.5 * x * x + d - d * v + d * std::log(v)) {
+      double g = d * v;
+      if (k < 1.0) g = g * std::pow(unit_open(w[2]), 1.0 / k);
+      return g;
+    }
+  }
 }
 
 struct SimBase {
@@ -215,6 +250,7 @@ struct Sim : SimBase {
   std::vector<Real> V, J;  // J as [4][N]
   std::vector<int32_t> ref;
   std::vector<Real> Ibg;   // background OU current
+  std::vector<Real> fext;  // per-neuron I_ext factor (1 where homogeneous)
 
   int32_t class_of(int32_t i) const {
     int32_t r = region_of[(size_t)i];
@@ -264,7 +300,12 @@ struct Sim : SimBase {
         }
         Real leak = p.gL * (v - p.VL);
         Real I = Isyn - leak;
-        I = I + p.Iext;
+        if (p.het) {
+          Real ie = p.Iext * fext[(size_t)i];
+          I = I + ie;
+        } else {
+          I = I + p.Iext;
+        }
         if (p.ou_on) I = I + Ibg[(size_t)i];
         Real dV = I * p.dtC;
         Real vn = v + dV;
@@ -413,12 +454,19 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
     c.ou_mu = (Real)p.ou_mu;
     c.ou_k = c.ou_on ? (Real)(o->dt_ms / p.ou_tau) : (Real)0;
     c.ou_s = c.ou_on ? (Real)(p.ou_sigma * std::sqrt(2.0 * o->dt_ms / p.ou_tau)) : (Real)0;
+    if (!(p.iext_shape >= 0.0)) { *err = -1; delete s; return nullptr; }
+    c.het = p.iext_shape > 0.0 ? 1 : 0;
   }
   s->V.resize((size_t)N);
   s->J.assign((size_t)4 * N, (Real)0);
   s->ref.assign((size_t)N, 0);
   s->Ibg.resize((size_t)N);
   for (int32_t i = 0; i < N; ++i) s->Ibg[(size_t)i] = s->rc[(size_t)s->region_of[(size_t)i]].ou_mu;
+  s->fext.assign((size_t)N, (Real)1);
+  for (int32_t i = 0; i < N; ++i) {
+    const double k = regs[s->region_of[(size_t)i]].iext_shape;
+    if (k > 0.0) s->fext[(size_t)i] = (Real)(gamma_draw(k, o->seed, o->net_id, i) / k);
+  }
   // initial V uniform in [V_reset, V_th) from the neuron's own Philox word
   for (int32_t i = 0; i < N; ++i) {
     const RegionConst<Real>& p = s->rc[(size_t)s->region_of[(size_t)i]];
@@ -469,6 +517,10 @@ void og_read_ibg(void* h, double* I) { ((SimBase*)h)->read_ibg(I); }
 void og_set_ibg(void* h, const double* I) { ((SimBase*)h)->set_ibg(I); }
 // the Box-Muller normal the OU current draws from a Philox word
 double og_box_muller(uint64_t w) { return box_muller(w); }
+// Gamma(k, 1) as drawn for neuron i's injected-current factor
+double og_gamma_draw(double k, uint64_t seed, uint64_t net_id, int64_t i) {
+  return gamma_draw(k, seed, net_id, i);
+}
 
 // info: [N, R, D, S, step, events, spikes, raster_len, bold_samples, bins_done]
 void og_info(void* h, int64_t* info) {

@@ -446,3 +446,32 @@ def test_ou_current_enters_the_membrane_bracket_with_its_old_value():
     s.step(1)
     expect = V0 + (0.1 / p["C"]) * (-p["gL"] * (V0 - p["VL"]) + p["I_ext"] + I0)
     assert np.allclose(s.state()[0], expect, rtol=1e-13, atol=1e-12)
+
+
+# -------------------------------------------- heterogeneous injected current --
+@pytest.mark.parametrize("k", [0.5, 2.5, 9.0])
+def test_gamma_draws_follow_the_gamma_law(k):
+    """Per-neuron I_ext factors (Methods: I_ext,i Gamma distributed):
+    Marsaglia-Tsang draws against scipy's Gamma(k) (KS), mean and variance k
+    (k < 1 goes through G(k + 1) U^(1/k))."""
+    stats = pytest.importorskip("scipy.stats")
+    n = 20000
+    g = np.array([oracle.gamma_draw(k, 11, 3, i) for i in range(n)])
+    assert abs(g.mean() - k) < 5.0 * math.sqrt(k / n)
+    assert abs(g.var() / k - 1.0) < 5.0 * math.sqrt((2.0 + 6.0 / k) / n)
+    assert stats.kstest(g, stats.gamma(k).cdf).pvalue > 1e-3
+
+
+def test_heterogeneous_current_enters_the_membrane_bracket():
+    """With iext_shape k, neuron i's injected current is I_ext * G_i / k
+    inside the dt/C bracket."""
+    N, k = 16, 3.0
+    p = synth.default_region_params(I_ext=0.4, iext_shape=k, drive_rate_hz=0.0, Vth=100.0)
+    s = oracle.Sim(_empty_graph(N), p, seed=21, net_id=2, precision=64)
+    V0 = np.linspace(-70.0, -52.0, N)
+    s.set_state(V=V0, J=np.zeros((4, N)), ref=np.zeros(N, np.int32))
+    s.step(1)
+    f = np.array([oracle.gamma_draw(k, 21, 2, i) / k for i in range(N)])
+    expect = V0 + (0.1 / p["C"]) * (-p["gL"] * (V0 - p["VL"]) + p["I_ext"] * f)
+    assert np.allclose(s.state()[0], expect, rtol=1e-13, atol=1e-12)
+    assert f.std() > 0.1  # the factors differ between neurons
