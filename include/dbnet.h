@@ -99,12 +99,18 @@ typedef struct {
  *                                  device); added after I_ext inside the dt/C
  *                                  bracket with its value before the step; it
  *                                  starts at mu.  Off when ou_mu = ou_sigma = 0;
- *                                  else ou_tau > 0 and ou_sigma >= 0. */
+ *                                  else ou_tau > 0 and ou_sigma >= 0.
+ *   iext_shape                     > 0: heterogeneous injected current (Methods:
+ *                                  I_ext,i Gamma distributed): neuron i receives
+ *                                  I_ext * G_i / k, G_i ~ Gamma(k = iext_shape, 1)
+ *                                  drawn once at create (Marsaglia-Tsang on its
+ *                                  Philox words of stream 5, FP64); 0: I_ext. */
 typedef struct {
   double C, gL, VL, Vth, Vreset, Tref;
   double Vu[4], tau_u[4], g_u[4];
   double I_ext, drive_rate_hz, drive_K, w_ext;
   double ou_mu, ou_sigma, ou_tau;
+  double iext_shape;
 } dbnet_region_params_t;
 
 /* Run options.
@@ -235,6 +241,18 @@ void dbnet_destroy(dbnet_t* h);
 #define DBENS_DIFFUSION 0 /* one observer per region, fused with weight gamma */
 #define DBENS_GLOBAL 1    /* one observer of all regions (textbook EnKF) */
 
+/* What each of a region's two log scales multiplies (Supplementary Sec. 6:
+ * the maximal conductances for resting-state data, the injected current for
+ * task data).  A scale family keeps its shape under cdf^-1(cdf(.; old); new),
+ * so the region's value is base * exp(theta). */
+#define DBENS_T_DEFAULT 0 /* slot 0: g_AMPA, slot 1: g_GABA_A */
+#define DBENS_T_AMPA 1
+#define DBENS_T_NMDA 2
+#define DBENS_T_GABA_A 3
+#define DBENS_T_GABA_B 4
+#define DBENS_T_IEXT 5    /* the region's injected current (task variant) */
+#define DBENS_T_NONE (-1) /* carried in the state, scales nothing */
+
 typedef struct {
   double obs_var;     /* Gamma_o: observation noise variance of every BOLD signal */
   double gamma;       /* fusion coefficient of Supplementary Algorithm 3 */
@@ -243,10 +261,11 @@ typedef struct {
   double theta_hi;
   double floor;       /* f, v, q are kept >= floor after an analysis */
   int32_t mode;       /* DBENS_DIFFUSION or DBENS_GLOBAL */
+  int32_t target[2];  /* DBENS_T_* of the two log scales (two distinct targets) */
 } dbens_enkf_t;
 
 /* base: [R] parameters before scaling; log_scale_init: [M][R][2] initial
- * theta (AMPA, GABA_A).  Errors as dbnet_create. */
+ * theta of the two targets.  Errors as dbnet_create. */
 int ens_create(const dbnet_graph_t* graph, const dbnet_region_params_t* base,
                int32_t n_members, const double* log_scale_init,
                const dbnet_options_t* options, const dbens_enkf_t* enkf,

@@ -151,9 +151,45 @@ void check_params(const dbnet_region_params_t& p, double dt) {
     raise(DBNET_EINVAL, "ou_mu must be finite and ou_sigma finite and >= 0");
   if ((p.ou_mu != 0.0 || p.ou_sigma != 0.0) && !(p.ou_tau > 0 && finite(p.ou_tau)))
     raise(DBNET_EINVAL, "ou_tau must be > 0 when the OU current is on");
+  if (!(p.iext_shape >= 0) || !finite(p.iext_shape))
+    raise(DBNET_EINVAL, "iext_shape must be finite and >= 0");
 }
 
 static bool ou_on(const dbnet_region_params_t& p) { return p.ou_mu != 0.0 || p.ou_sigma != 0.0; }
+static int32_t ext_bits(const dbnet_region_params_t& p) {
+  return (ou_on(p) ? kExtOU : 0) | (p.iext_shape > 0.0 ? kExtHet : 0);
+}
+
+// Per-neuron injected-current factor G / k, G ~ Gamma(k, 1), for local
+// neuron i: the Marsaglia-Tsang method (ACM TOMS 26(3), 2000) on the
+// neuron's Philox words of stream 5 -- attempt a uses counter (0, i, 5, a):
+// word 0 gives a Box-Muller normal, word 1 the acceptance uniform, word 2
+// (k < 1) the uniform of G(k) = G(k + 1) U^(1/k) -- in FP64.
+static double unit_open(unsigned long long w) { return ((double)(w >> 32) + 1.0) * std::ldexp(1.0, -32); }
+static double normal_of(unsigned long long w) {
+  const double u1 = unit_open(w);
+  const double u2 = (double)(w & 0xFFFFFFFFull) * std::ldexp(1.0, -32);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * 3.14159265358979323846 * u2);
+}
+static double gamma_of(double k, unsigned long long seed, unsigned long long net_id, int64_t i) {
+  const double kk = k < 1.0 ? k + 1.0 : k;
+  const double d = kk - 1.0 / 3.0;
+  const double c = 1.0 / std::sqrt(9.0 * d);
+  for (unsigned long long a = 0;; ++a) {
+    unsigned long long w[4] = {0ull, (unsigned long long)i, 5ull, a};
+    philox4x64_10(w, seed, net_id);
+    const double x = normal_of(w[0]);
+    const double t = 1.0 + c * x;
+    if (t <= 0.0) continue;
+    const double v = t * t * t;
+    const double u = unit_open(w[1]);
+    if (std::log(u) < 0.5 * x * x + d - d * v + d * std::log(v)) {
+      double gm = d * v;
+      if (k < 1.0) gm = gm * std::pow(unit_open(w[2]), 1.0 / k);
+      return gm;
+    }
+  }
+}
 
 // Thresholds of the integer-inversion Poisson draw: floor(P(X <= k) 2^32) for
 // the leading k (at most 16) whose value stays below 2^32.
@@ -194,8 +230,8 @@ RegionConst region_const(const dbnet_region_params_t& p, double dt, int S, int32
   c.start = start;
   c.end = end;
   c.exc_end = exc_end;
+  c.ext = ext_bits(p);
   if (ou_on(p)) {
-    c.ou_on = 1;
     c.ou_mu = (float)p.ou_mu;
     c.ou_k = (float)(dt / p.ou_tau);
     c.ou_s = (float)(p.ou_sigma * std::sqrt(2.0 * dt / p.ou_tau));
@@ -252,10 +288,10 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     regions += sp.graph->R;
     dmax_all = std::max(dmax_all, sp.graph->max_delay);
   }
-  bool any_ou = false;
+  bool any_ext = false;
   for (const auto& sp : specs)
-    for (const auto& p : sp.params) any_ou = any_ou || ou_on(p);
-  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream, any_ou);
+    for (const auto& p : sp.params) any_ext = any_ext || ext_bits(p) != 0;
+  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream, any_ext);
   int64_t t = 0;
   int32_t r = 0;
   for (int k = 0; k < n; ++k) {
@@ -268,7 +304,7 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
 }
 
 void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
-                       const dbnet_options_t& common, void* user_stream, bool any_ou) {
+                       const dbnet_options_t& common, void* user_stream, bool any_ext) {
   if (user_stream) {
     stream = (cudaStream_t)user_stream;
     own_stream = false;
@@ -289,9 +325,11 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   V.alloc(stride);
   J.alloc(4 * stride);
   Ibg.alloc(stride);
+  fext.alloc(stride);
   ref.alloc(stride);
   acc.alloc(stride);
   CK(cudaMemsetAsync(Ibg.p, 0, sizeof(float) * stride, stream));
+  CK(cudaMemsetAsync(fext.p, 0, sizeof(float) * stride, stream));  // read only where kExtHet
   CK(cudaMemsetAsync(V.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
   CK(cudaMemsetAsync(ref.p, 0, stride, stream));
@@ -350,7 +388,8 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev.V = V.p;
   dev.J = J.p;
   dev.Ibg = Ibg.p;
-  dev.any_ou = any_ou ? 1 : 0;
+  dev.fext = fext.p;
+  dev.any_ext = any_ext ? 1 : 0;
   dev.ref = ref.p;
   dev.acc = acc.p;
   dev.stride = stride;
@@ -430,8 +469,9 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
   d.seg_kind = g.seg_kind;
   d.dmax = g.max_delay;
   d.seg_stride = g.seg_stride;
-  for (const auto& p : sp.params) d.ou = d.ou || ou_on(p);
-  if (d.ou && !dev.any_ou) raise(DBNET_EUNSUPPORTED, "this engine was built without the OU current");
+  for (const auto& p : sp.params) d.ext |= ext_bits(p);
+  if (d.ext && !dev.any_ext)
+    raise(DBNET_EUNSUPPORTED, "this engine was built without the OU current or injected-current factors");
   d.region_offsets = g.ro.p;
   d.rc = ih.rc.p;
   d.bold = ih.bold.p;
@@ -491,6 +531,17 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
   CK(cudaMemsetAsync(ylast.p + rbase, 0, sizeof(double) * g.R, stream));
   CK(cudaMemsetAsync(closed.p + rbase, 0, sizeof(long long) * g.R, stream));
   launch_init_state(dev, k, nt, first_tile, stream);
+  if (ih.desc.ext & kExtHet) {  // per-neuron injected-current factors
+    ih.stage_fext.assign((size_t)g.N, 1.0f);
+    for (int32_t r = 0; r < g.R; ++r) {
+      const double kr = sp.params[(size_t)r].iext_shape;
+      if (kr > 0.0)
+        for (int32_t i = g.ro_h[r]; i < g.ro_h[r + 1]; ++i)
+          ih.stage_fext[(size_t)i] = (float)(gamma_of(kr, sp.opt.seed, sp.net_id, i) / kr);
+    }
+    CK(cudaMemcpyAsync(fext.p + (int64_t)first_tile * kTile, ih.stage_fext.data(),
+                       sizeof(float) * g.N, cudaMemcpyHostToDevice, stream));
+  }
   CK(cudaGetLastError());
 }
 

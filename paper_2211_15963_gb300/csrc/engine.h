@@ -39,6 +39,36 @@
 
 namespace dbn {
 
+// Philox4x64-10 (Salmon et al., SC'11): ten rounds, two 64x64->128 products
+// per round with the published multipliers; the key advances by the Weyl
+// constants after each round.  Host and device (the host draws the
+// per-neuron injected-current factors at create).
+__host__ __device__ __forceinline__ unsigned long long mulhi64(unsigned long long a,
+                                                               unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                                       unsigned long long k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+    unsigned long long hi0 = mulhi64(m0, c[0]), lo0 = m0 * c[0];
+    unsigned long long hi1 = mulhi64(m1, c[2]), lo1 = m1 * c[2];
+    unsigned long long n0 = hi1 ^ c[1] ^ k0;
+    unsigned long long n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+}
+
 constexpr int kTile = 1024;         // neurons per update block
 constexpr int kUpdThreads = 256;    // four neurons per thread
 constexpr int kDelThreads = 256;
@@ -58,7 +88,11 @@ struct alignas(16) RegionConst {
                                        // local neuron range [start, end)
   uint32_t thr[kMaxThr];             // Poisson inversion thresholds, non-decreasing
   float ou_mu, ou_k, ou_s;           // background OU current: mu, dt/tau,
-  int32_t ou_on;                     //   sigma sqrt(2 dt/tau); 1 when on
+  int32_t ext;                       //   sigma sqrt(2 dt/tau); kExt* bits
+};
+enum : int32_t {
+  kExtOU = 1,    // background OU current
+  kExtHet = 2,   // per-neuron injected-current factor
 };
 
 enum : int32_t {
@@ -89,7 +123,7 @@ struct alignas(16) InstDesc {
   uint32_t tmask;
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;
-  int32_t seg_kind, dmax, seg_stride, ou;  // ou: some region has the OU current
+  int32_t seg_kind, dmax, seg_stride, ext;  // ext: kExt* bits of any region
   double h_bw, z_scale, kappa, gamma, tau, alpha, rho, V0;
 };
 
@@ -120,6 +154,7 @@ struct EngineDev {
   float* V;
   float* J;
   float* Ibg;            // background OU current per neuron
+  float* fext;           // per-neuron injected-current factor (1 where homogeneous)
   uint8_t* ref;
   int2* acc;
   int64_t stride;
@@ -142,7 +177,7 @@ struct EngineDev {
   unsigned int* flags;
   int32_t D;
   int32_t n_inst, n_tiles, total_R;
-  int32_t any_ou;        // launch the update with the OU current
+  int32_t any_ext;       // launch the update variant with the kExt* terms
 };
 
 // Launchers (kernels.cu)

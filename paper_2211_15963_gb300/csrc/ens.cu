@@ -217,11 +217,16 @@ __global__ void k_normals(double* out, int n, unsigned long long seed, unsigned 
   out[i] = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
 
-// theta <- clip(theta + rw_sigma xi) and the members' scaled conductances:
-// g_AMPA = base_AMPA exp(theta_AMPA), g_GABA_A = base_GABA_A exp(theta_GABA_A).
+// theta <- clip(theta + rw_sigma xi) and the members' scaled targets:
+// value = base exp(theta) for each slot's target (a conductance or I_ext).
+__device__ __forceinline__ void set_target(RegionConst& rc, int target, float v) {
+  if (target == DBENS_T_IEXT) rc.Iext = v;
+  else if (target >= DBENS_T_AMPA && target <= DBENS_T_GABA_B) rc.g[target - DBENS_T_AMPA] = v;
+}
+
 __global__ void k_walk_rescale(double* theta, const double* xi, const double* base_g,
                                const InstDesc* insts, int M, int R, double rw, double lo,
-                               double hi) {
+                               double hi, int t0, int t1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * R) return;
   const int m = i / R, r = i % R;
@@ -230,8 +235,8 @@ __global__ void k_walk_rescale(double* theta, const double* xi, const double* ba
   theta[2 * i] = ta;
   theta[2 * i + 1] = tg;
   RegionConst* rc = const_cast<RegionConst*>(insts[m].rc);
-  rc[r].g[0] = (float)(base_g[2 * r] * exp(ta));
-  rc[r].g[2] = (float)(base_g[2 * r + 1] * exp(tg));
+  set_target(rc[r], t0, (float)(base_g[2 * r] * exp(ta)));
+  set_target(rc[r], t1, (float)(base_g[2 * r + 1] * exp(tg)));
 }
 
 inline int blocks(int64_t n, int t = 128) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -245,6 +250,7 @@ struct dbens {
   std::unique_ptr<Engine> eng;
   int M = 0, R = 0;
   dbens_enkf_t enkf{};
+  int target[2] = {DBENS_T_AMPA, DBENS_T_GABA_A};  // resolved DBENS_T_* of the two slots
   uint64_t seed = 0, net_id0 = 0;
   unsigned long long n_analyses = 0;
   DevBuf<double> theta, base_g, X, A, mu, K, nu, S, P, eps, xi, yobs;
@@ -275,12 +281,33 @@ int ens_guard(dbens* h, F&& f) {
   }
 }
 
+int resolve_target(const dbens_enkf_t& k, int slot) {
+  if (k.target[slot] != DBENS_T_DEFAULT) return k.target[slot];
+  return slot == 0 ? DBENS_T_AMPA : DBENS_T_GABA_A;
+}
+
+double target_value(const dbnet_region_params_t& p, int target) {
+  if (target == DBENS_T_IEXT) return p.I_ext;
+  if (target >= DBENS_T_AMPA && target <= DBENS_T_GABA_B) return p.g_u[target - DBENS_T_AMPA];
+  return 0.0;
+}
+
+void scale_target(dbnet_region_params_t& p, int target, double v) {
+  if (target == DBENS_T_IEXT) p.I_ext = v;
+  else if (target >= DBENS_T_AMPA && target <= DBENS_T_GABA_B) p.g_u[target - DBENS_T_AMPA] = v;
+}
+
 void check_enkf(const dbens_enkf_t& k) {
   if (!(k.obs_var > 0) || !std::isfinite(k.obs_var)) raise(DBNET_EINVAL, "obs_var must be > 0");
   if (!(k.gamma >= 0 && k.gamma <= 1)) raise(DBNET_EINVAL, "gamma must be in [0, 1]");
   if (!(k.rw_sigma >= 0) || !std::isfinite(k.rw_sigma)) raise(DBNET_EINVAL, "rw_sigma must be >= 0");
   if (!(k.theta_lo <= k.theta_hi) || !std::isfinite(k.theta_lo) || !std::isfinite(k.theta_hi))
     raise(DBNET_EINVAL, "theta bounds must be finite with lo <= hi");
+  for (int sl = 0; sl < 2; ++sl)
+    if (k.target[sl] < DBENS_T_NONE || k.target[sl] > DBENS_T_IEXT)
+      raise(DBNET_EINVAL, "target must be one of DBENS_T_*");
+  const int a = resolve_target(k, 0), b = resolve_target(k, 1);
+  if (a == b && a != DBENS_T_NONE) raise(DBNET_EINVAL, "the two log scales need distinct targets");
   if (!(k.floor > 0)) raise(DBNET_EINVAL, "floor must be > 0");
   if (k.mode != DBENS_DIFFUSION && k.mode != DBENS_GLOBAL) raise(DBNET_EINVAL, "unknown EnKF mode");
 }
@@ -318,8 +345,10 @@ int ens_create(const dbnet_graph_t* graph, const dbnet_region_params_t* base, in
         const double* t = log_scale_init + ((size_t)m * R + r) * 2;
         const double ta = std::min(std::max(t[0], enkf->theta_lo), enkf->theta_hi);
         const double tg = std::min(std::max(t[1], enkf->theta_lo), enkf->theta_hi);
-        sp.params[(size_t)r].g_u[0] = base[r].g_u[0] * std::exp(ta);
-        sp.params[(size_t)r].g_u[2] = base[r].g_u[2] * std::exp(tg);
+        scale_target(sp.params[(size_t)r], resolve_target(*enkf, 0),
+                     target_value(base[r], resolve_target(*enkf, 0)) * std::exp(ta));
+        scale_target(sp.params[(size_t)r], resolve_target(*enkf, 1),
+                     target_value(base[r], resolve_target(*enkf, 1)) * std::exp(tg));
       }
       sp.opt = *options;
       sp.net_id = options->net_id + (uint64_t)m;
@@ -348,9 +377,11 @@ int ens_create(const dbnet_graph_t* graph, const dbnet_region_params_t* base, in
     std::vector<double> th((size_t)M * R * 2), bg((size_t)R * 2);
     for (size_t i = 0; i < th.size(); ++i)
       th[i] = std::min(std::max(log_scale_init[i], enkf->theta_lo), enkf->theta_hi);
+    h->target[0] = resolve_target(*enkf, 0);
+    h->target[1] = resolve_target(*enkf, 1);
     for (int r = 0; r < R; ++r) {
-      bg[2 * r] = base[r].g_u[0];
-      bg[2 * r + 1] = base[r].g_u[2];
+      bg[2 * r] = target_value(base[r], h->target[0]);
+      bg[2 * r + 1] = target_value(base[r], h->target[1]);
     }
     Engine& e = *h->eng;
     CK(cudaMemcpyAsync(h->theta.p, th.data(), sizeof(double) * th.size(), cudaMemcpyHostToDevice, e.stream));
@@ -403,7 +434,8 @@ int ens_assimilate(dbens_t* h, const double* y_obs, const double* eps_obs, const
                                                          h->enkf.theta_lo, h->enkf.theta_hi,
                                                          h->enkf.floor);
     k_walk_rescale<<<blocks(M * R), 128, 0, s>>>(h->theta.p, h->xi.p, h->base_g.p, e.desc.p, M, R,
-                                                  h->enkf.rw_sigma, h->enkf.theta_lo, h->enkf.theta_hi);
+                                                  h->enkf.rw_sigma, h->enkf.theta_lo, h->enkf.theta_hi,
+                                                  h->target[0], h->target[1]);
     CK(cudaGetLastError());
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, h->bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -198,6 +198,7 @@ struct InstHost {
   std::vector<int4> stage_ti;
   std::vector<int32_t> stage_ri;
   std::vector<double> stage_bw;
+  std::vector<float> stage_fext;
   InstDyn stage_dyn{};
 };
 
@@ -206,7 +207,7 @@ struct Engine {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<InstHost> inst;
-  DevBuf<float> V, J, Ibg;
+  DevBuf<float> V, J, Ibg, fext;
   DevBuf<uint8_t> ref;
   DevBuf<int2> acc;
   DevBuf<InstDesc> desc;
@@ -248,9 +249,10 @@ struct Engine {
   void init(const std::vector<InstSpec>& specs, void* user_stream);
   // Empty capacity for instances placed later: every tile and region slot
   // starts unused (the kernels skip it); D = longest delay + 1.
-  // any_ou: launch the update with the background OU current.
+  // any_ext: launch the update variant with the OU current and the
+  // per-neuron injected-current factors.
   void init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
-                 const dbnet_options_t& common, void* user_stream, bool any_ou);
+                 const dbnet_options_t& common, void* user_stream, bool any_ext);
   // Put instance k on tiles [first_tile, +tiles of its graph) and region
   // slots [rbase, +R): its constants, buffers and initial state; its step 0
   // is the next iteration enqueued, and it stops after n_end steps.

@@ -33,26 +33,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Philox4x64-10 (Salmon et al., SC'11): ten rounds, two 64x64->128 products
-// per round with the published multipliers; the key advances by the Weyl
-// constants after each round.
-__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
-                                              unsigned long long k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
-    unsigned long long hi0 = __umul64hi(m0, c[0]), lo0 = m0 * c[0];
-    unsigned long long hi1 = __umul64hi(m1, c[2]), lo1 = m1 * c[2];
-    unsigned long long n0 = hi1 ^ c[1] ^ k0;
-    unsigned long long n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-    k0 += 0x9E3779B97F4A7C15ull;
-    k1 += 0xBB67AE8584CAA73Bull;
-  }
-}
+// (philox4x64_10 is in engine.h: the host draws with it too)
 
 __device__ __forceinline__ int find_region(const int32_t* __restrict__ ro, int R, int32_t li) {
   int lo = 0, hi = R - 1;
@@ -99,7 +80,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_init_state(EngineDev e, int ins
       const float u = __fmul_rn(__ull2float_rn(c[k] >> 40), 5.9604644775390625e-08f);  // 2^-24
       const float span = __fsub_rn(p.Vth, p.Vreset);
       v4[k] = __fadd_rn(p.Vreset, __fmul_rn(span, u));
-      if (p.ou_on) b4[k] = p.ou_mu;
+      if (p.ext & kExtOU) b4[k] = p.ou_mu;
     }
   }
   *reinterpret_cast<float4*>(e.V + gi0) = make_float4(v4[0], v4[1], v4[2], v4[3]);
@@ -157,8 +138,9 @@ __device__ __forceinline__ float normal_from_word(unsigned long long w) {
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
-// OU: also integrate the background OU current (instances with d.ou).
-template <bool OU>
+// EXT: also the kExt* terms of the instances that have them: the background
+// OU current and the per-neuron injected-current factor.
+template <bool EXT>
 __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef sr) {
   __shared__ RegionConst s_rc[kTileRegions];
   __shared__ uint32_t s_wtot[kUpdThreads / 32];
@@ -176,8 +158,11 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
 #pragma unroll
   for (int u = 0; u < 4; ++u) J4[u] = __ldcs(reinterpret_cast<const float4*>(e.J + u * e.stride + gi0));
   const uchar4 rf = __ldcs(reinterpret_cast<const uchar4*>(e.ref + gi0));
-  float4 B4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (OU) B4 = __ldcs(reinterpret_cast<const float4*>(e.Ibg + gi0));
+  float4 B4 = make_float4(0.f, 0.f, 0.f, 0.f), F4 = make_float4(1.f, 1.f, 1.f, 1.f);
+  if (EXT) {
+    B4 = __ldcs(reinterpret_cast<const float4*>(e.Ibg + gi0));
+    F4 = __ldg(reinterpret_cast<const float4*>(e.fext + gi0));
+  }
   const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
   const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
 
@@ -209,8 +194,9 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     unsigned long long x[4] = {(unsigned long long)n, (unsigned long long)(li0 >> 2), 0ull, 0ull};
     philox4x64_10(x, d.seed, d.net_id);
     float ib[4] = {B4.x, B4.y, B4.z, B4.w};
+    const float fe[4] = {F4.x, F4.y, F4.z, F4.w};
     unsigned long long xo[4] = {0ull, 0ull, 0ull, 0ull};
-    if (OU && d.ou) {  // the OU noise: stream 4
+    if (EXT && (d.ext & kExtOU)) {  // the OU noise: stream 4
       xo[0] = (unsigned long long)n;
       xo[1] = (unsigned long long)(li0 >> 2);
       xo[2] = 4ull;
@@ -257,14 +243,15 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
       }
       const float leak = __fmul_rn(M.y, __fsub_rn(vk, M.z));
       float I = __fsub_rn(Isyn, leak);
-      I = __fadd_rn(I, Q.y);
-      float4 OUc = make_float4(0.f, 0.f, 0.f, 0.f);  // mu, dt/tau, sigma sqrt(2 dt/tau), on
-      if (OU && d.ou) {
-        OUc = *reinterpret_cast<const float4*>(&p.ou_mu);
-        if (__float_as_int(OUc.w)) I = __fadd_rn(I, ib[k]);  // I_bg before this step
-      }
+      float4 OUc = make_float4(0.f, 0.f, 0.f, 0.f);  // mu, dt/tau, sigma sqrt(2 dt/tau), bits
+      if (EXT && d.ext) OUc = *reinterpret_cast<const float4*>(&p.ou_mu);
+      const int xb = __float_as_int(OUc.w);
+      // injected current, scaled by the neuron's factor where heterogeneous
+      const float ie = (EXT && (xb & kExtHet)) ? __fmul_rn(Q.y, fe[k]) : Q.y;
+      I = __fadd_rn(I, ie);
+      if (EXT && (xb & kExtOU)) I = __fadd_rn(I, ib[k]);  // I_bg before this step
       const float vn = __fadd_rn(vk, __fmul_rn(I, M.x));
-      if (OU && d.ou && __float_as_int(OUc.w)) {  // Eq. 1, Euler-Maruyama
+      if (EXT && (xb & kExtOU)) {  // Eq. 1, Euler-Maruyama
         const float xi = normal_from_word(xo[k]);
         const float t1 = __fmul_rn(__fsub_rn(OUc.x, ib[k]), OUc.y);
         ib[k] = __fadd_rn(ib[k], t1);
@@ -298,7 +285,8 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     __stcs(reinterpret_cast<uchar4*>(e.ref + gi0),
            make_uchar4((unsigned char)rr[0], (unsigned char)rr[1], (unsigned char)rr[2],
                        (unsigned char)rr[3]));
-    if (OU && d.ou) __stcs(reinterpret_cast<float4*>(e.Ibg + gi0), make_float4(ib[0], ib[1], ib[2], ib[3]));
+    if (EXT && (d.ext & kExtOU))
+      __stcs(reinterpret_cast<float4*>(e.Ibg + gi0), make_float4(ib[0], ib[1], ib[2], ib[3]));
   }
 
   // ---- spikes: one ring append, spike and raster count per block ---------
@@ -658,7 +646,7 @@ void launch_init_state(const EngineDev& e, int inst, int n_tiles_inst, int first
 }
 
 void launch_update(const EngineDev& e, StepRef sr, cudaStream_t s) {
-  if (e.any_ou) k_update<true><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+  if (e.any_ext) k_update<true><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
   else k_update<false><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
 }
 

@@ -184,8 +184,9 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     check_options(*options);
     for (int32_t r = 0; r < R; ++r) {
       check_params(params[r], options->dt_ms);
-      if (params[r].ou_mu != 0.0 || params[r].ou_sigma != 0.0)
-        raise(DBNET_EUNSUPPORTED, "the allocation-free entry point has no background OU state");
+      if (params[r].ou_mu != 0.0 || params[r].ou_sigma != 0.0 || params[r].iext_shape != 0.0)
+        raise(DBNET_EUNSUPPORTED,
+              "the allocation-free entry point has no OU state or injected-current factors");
     }
 
     cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -47,7 +47,7 @@ class dbnet_region_params_t(ctypes.Structure):
     _fields_ = [("C", _d), ("gL", _d), ("VL", _d), ("Vth", _d), ("Vreset", _d), ("Tref", _d),
                 ("Vu", _d * 4), ("tau_u", _d * 4), ("g_u", _d * 4), ("I_ext", _d),
                 ("drive_rate_hz", _d), ("drive_K", _d), ("w_ext", _d),
-                ("ou_mu", _d), ("ou_sigma", _d), ("ou_tau", _d)]
+                ("ou_mu", _d), ("ou_sigma", _d), ("ou_tau", _d), ("iext_shape", _d)]
 
 
 class dbnet_options_t(ctypes.Structure):
@@ -99,7 +99,12 @@ DBSRV_QUEUED, DBSRV_RUNNING, DBSRV_DONE, DBSRV_FAILED = 0, 1, 2, 3
 
 class dbens_enkf_t(ctypes.Structure):
     _fields_ = [("obs_var", _d), ("gamma", _d), ("rw_sigma", _d), ("theta_lo", _d),
-                ("theta_hi", _d), ("floor", _d), ("mode", _i32)]
+                ("theta_hi", _d), ("floor", _d), ("mode", _i32), ("target", _i32 * 2)]
+
+
+# what each of a region's two log scales multiplies
+DBENS_T_DEFAULT, DBENS_T_AMPA, DBENS_T_NMDA, DBENS_T_GABA_A, DBENS_T_GABA_B, DBENS_T_IEXT = range(6)
+DBENS_T_NONE = -1
 
 
 _SIGS = {
@@ -234,6 +239,7 @@ def region_params(p: dict) -> dbnet_region_params_t:
     r.ou_mu = float(p.get("ou_mu", 0.0))
     r.ou_sigma = float(p.get("ou_sigma", 0.0))
     r.ou_tau = float(p.get("ou_tau", 10.0))
+    r.iext_shape = float(p.get("iext_shape", 0.0))
     for k in ("Vu", "tau_u", "g_u"):
         arr = getattr(r, k)
         for u in range(4):
@@ -446,8 +452,11 @@ def dbnet_run_noalloc(n_neurons, region_offsets, n_exc, row_ptr, col, weight_bf1
 
 # -------------------------------------------------------------- ensemble ----
 def enkf_options(obs_var=1e-6, gamma=0.5, rw_sigma=0.02, theta_lo=-0.6931471805599453,
-                 theta_hi=0.6931471805599453, floor=1e-2, mode=DBENS_DIFFUSION) -> dbens_enkf_t:
-    return dbens_enkf_t(obs_var, gamma, rw_sigma, theta_lo, theta_hi, floor, mode)
+                 theta_hi=0.6931471805599453, floor=1e-2, mode=DBENS_DIFFUSION,
+                 target=(DBENS_T_DEFAULT, DBENS_T_DEFAULT)) -> dbens_enkf_t:
+    k = dbens_enkf_t(obs_var, gamma, rw_sigma, theta_lo, theta_hi, floor, mode)
+    k.target[0], k.target[1] = int(target[0]), int(target[1])
+    return k
 
 
 def ens_create(graph, base_params, n_members: int, log_scale_init, options=None, enkf=None,

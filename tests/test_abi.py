@@ -133,3 +133,15 @@ def test_ou_parameters_are_validated(lib):
     _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(ou_mu=0.5, ou_tau=0.0))
     _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(ou_sigma=-0.1, ou_tau=5.0))
     _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(ou_mu=float("nan"), ou_tau=5.0))
+
+
+def test_enkf_targets_are_validated(lib):
+    g = _tiny_graph()
+    p = synth.default_region_params()
+    th = np.zeros((3, 2, 2))
+    for tgt in [(7, 0), (-2, 0), (dbnet.DBENS_T_IEXT, dbnet.DBENS_T_IEXT),
+                (dbnet.DBENS_T_GABA_A, dbnet.DBENS_T_DEFAULT)]:
+        with pytest.raises(dbnet.DbnetError) as ei:
+            dbnet.ens_create(g, p, 3, th, {}, dbnet.enkf_options(target=tgt))
+        assert ei.value.code == dbnet.DBNET_EINVAL, tgt
+    _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(iext_shape=-1.0))

@@ -135,3 +135,77 @@ def test_twin_experiment_recovers_direction():
     assert abs(end - np.log(1.6)) < abs(start - np.log(1.6))
     hidden.close()
     ens.close()
+
+
+def _scaled(base, theta_m, targets):
+    """Region parameters with each target scaled by exp(theta) (math.exp, the
+    C library's, as the library uses at create)."""
+    from paper_2211_15963_gb300 import dbnet
+    out = []
+    for r, p in enumerate(base):
+        q = dict(p)
+        g = list(q["g_u"])
+        for sl, t in enumerate(targets):
+            f = math.exp(theta_m[r, sl])
+            if t == dbnet.DBENS_T_IEXT:
+                q["I_ext"] = q["I_ext"] * f
+            elif t != dbnet.DBENS_T_NONE:
+                g[t - dbnet.DBENS_T_AMPA] = g[t - dbnet.DBENS_T_AMPA] * f
+        q["g_u"] = tuple(g)
+        out.append(q)
+    return out
+
+
+def test_task_variant_members_equal_single_networks():
+    """Task variant (Supp. Sec. 6): the scale multiplies the region's
+    injected current, heterogeneous per neuron (Gamma, k = 3); each member
+    (its own factors through its net_id) equals a single network."""
+    from paper_2211_15963_gb300 import dbnet
+    g = _graph()
+    base = [synth.default_region_params(I_ext=0.8 + 0.03 * r, iext_shape=3.0)
+            for r in range(g.n_regions)]
+    M = 3
+    targets = (dbnet.DBENS_T_IEXT, dbnet.DBENS_T_NONE)
+    theta = np.random.default_rng(4).uniform(LO, HI, (M, g.n_regions, 2))
+    opts = dict(seed=8, net_id=200, tr_ms=10.0, raster_capacity=1 << 20)
+    ens = dbnet.Ensemble(g, base, M, theta, opts, dict(target=targets))
+    ens.step(400)
+    for m in range(M):
+        net = dbnet.Network(g, _scaled(base, theta[m], targets), dict(opts, net_id=200 + m))
+        net.step(400)
+        for x, y in zip(ens.member_state(m), net.state()):
+            assert np.array_equal(x, y)
+        sa, sb = ens.member_spikes(m), net.spikes()
+        assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+        net.close()
+    ens.close()
+
+
+def test_task_twin_experiment_recovers_injected_current():
+    """A hidden member with every region's injected current scaled by 1.5
+    makes the observations; assimilating the injected-current scale moves
+    the ensemble toward it."""
+    from paper_2211_15963_gb300 import dbnet
+    g = _graph()
+    R = g.n_regions
+    base = [synth.default_region_params(I_ext=0.7) for _ in range(R)]
+    targets = (dbnet.DBENS_T_IEXT, dbnet.DBENS_T_NONE)
+    M, TR_STEPS = 24, 2000
+    rng = np.random.default_rng(6)
+    truth = np.zeros((R, 2))
+    truth[:, 0] = np.log(1.5)
+    opts = dict(seed=23, tr_ms=200.0, z_scale=50.0)
+    hidden = dbnet.Network(g, _scaled(base, truth, targets), dict(opts, net_id=998))
+    theta0 = rng.uniform(np.log(0.7), np.log(1.0), (M, R, 2))
+    ens = dbnet.Ensemble(g, base, M, theta0, dict(opts, net_id=0),
+                         dict(obs_var=1e-9, gamma=0.7, rw_sigma=0.01, theta_lo=LO, theta_hi=HI,
+                              target=targets))
+    start = theta0[:, :, 0].mean()
+    for _ in range(12):
+        hidden.step(TR_STEPS)
+        ens.step(TR_STEPS)
+        ens.assimilate(hidden.bold()[-1])
+    th, _, _ = ens.read()
+    assert abs(th[:, :, 0].mean() - np.log(1.5)) < abs(start - np.log(1.5))
+    hidden.close()
+    ens.close()

@@ -345,3 +345,22 @@ def test_ou_current_noise_statistics():
     assert r_64 > 1.0
     assert abs(r_gpu - r_64) / r_64 < 0.03, (r_gpu, r_64)
     assert abs(metrics.isi_cv(st, ids) - metrics.isi_cv(rs, rids)) < 0.03
+
+
+def test_heterogeneous_injected_current_bit_exact():
+    """Per-neuron Gamma-distributed injected current (Methods): the factors
+    the library draws at create equal the oracle's (both Marsaglia-Tsang on
+    Philox stream 5 in FP64), so the run is matched-FP32 bit-exact.  One
+    region heterogeneous (k = 0.7 takes the k < 1 branch), one with k = 4."""
+    g = synth.make_graph([2000, 1500], 80, 62, d_within=(1, 25), d_cross=(25, 70))
+    p = [synth.default_region_params(I_ext=0.9, iext_shape=0.7),
+         synth.default_region_params(I_ext=0.85, iext_shape=4.0)]
+    net = _net(g, p, seed=13, net_id=5)
+    o = oracle.Sim(g, p, seed=13, net_id=5, precision=32)
+    net.step(900)
+    o.step(900)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 500
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "heterogeneous I_ext")
