@@ -257,7 +257,7 @@ struct Sim : SimBase {
     return i < n_exc_end[(size_t)r] ? 0 : 1;
   }
 
-  // Supplementary Algorithm 2, line "update upcoming synaptic inputs": every
+  // Supplementary Algorithm 2, the push of a spike's synaptic input: every
   // out-edge of spiker j adds q(w) to the accumulator slot its delay selects.
   void scatter(int32_t j, int64_t step_n) {
     int32_t c = class_of(j);
