@@ -63,6 +63,17 @@ class _Spec(ctypes.Structure):
     ]
 
 
+class _ColumnSpec(ctypes.Structure):
+    _fields_ = [("n_voxels", ctypes.c_int32), ("n_pops", ctypes.c_int32),
+                ("pop_offset", ctypes.c_void_p), ("voxel_size", ctypes.c_int32),
+                ("n_exc", ctypes.c_int32), ("k_local", ctypes.c_void_p),
+                ("k_cc", ctypes.c_void_p), ("region_prob", ctypes.c_void_p),
+                ("d_within_min", ctypes.c_int32), ("d_within_max", ctypes.c_int32),
+                ("d_cross_min", ctypes.c_int32), ("d_cross_max", ctypes.c_int32),
+                ("w_mu", ctypes.c_double), ("w_sigma", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -72,6 +83,10 @@ def lib():
             L.synth_graph.restype = ctypes.c_int
             L.synth_graph.argtypes = [ctypes.POINTER(_Spec), ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+            L.synth_columns.restype = ctypes.c_int
+            L.synth_columns.argtypes = [ctypes.POINTER(_ColumnSpec), ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32]
             L.synth_region_matrix.restype = ctypes.c_int
             L.synth_region_matrix.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p]
@@ -164,6 +179,97 @@ def make_graph(sizes, k_in: int, seed: int, *, k_within: int | None = None,
         raise ValueError("synth_graph rejected the spec (code %d)" % rc)
     dmax = max(d_within[1], d_cross[1] if R > 1 else 0)
     return Graph(N, R, ro, n_exc, row_ptr, col, w, d, dmax)
+
+
+# ---------------------------------------------------------------------------
+# Cortical micro-columns.  Extended Data Table 3: the average number of
+# synapses a neuron of each postsynaptic population receives from each
+# presynaptic population of its column, and from other columns (CC).  Rows
+# and columns follow the populations below; the table has no e1 source
+# column (0 here) and blank cells are 0.
+COLUMN_POPS = ("e1", "i1", "e2/3", "i2/3", "e4", "i4", "e5", "i5", "e6", "i6")
+COLUMN_SOURCES = ("i1", "e2/3", "i2/3", "e4", "i4", "e5", "i5", "e6", "i6", "CC")
+COLUMN_TABLE = (  # rows: COLUMN_POPS; columns: COLUMN_SOURCES
+    (1323, 823, 200, 15, 1, 9, 0, 0, 0, 10133),
+    (901, 560, 149, 10, 1, 6, 0, 0, 0, 6899),
+    (133, 3554, 804, 881, 45, 431, 0, 136, 0, 1020),
+    (52, 1778, 532, 456, 29, 217, 0, 69, 0, 396),
+    (27, 417, 84, 1070, 782, 79, 8, 1686, 0, 1489),
+    (0, 168, 41, 628, 538, 36, 0, 1028, 0, 790),
+    (147, 2550, 176, 765, 99, 621, 596, 363, 0, 1591),
+    (0, 1357, 76, 380, 32, 375, 403, 129, 0, 214),
+    (2, 643, 46, 549, 196, 327, 126, 925, 597, 2609),
+    (0, 80, 8, 92, 3, 159, 11, 76, 499, 1794),
+)
+# Share of a column's neurons in layers 1, 2/3, 4, 5, 6.  The paper weights
+# layers by thickness but prints no values; these are generic proportions
+# (a thin, sparse layer 1), not the paper's.
+LAYER_FRACTION = (0.015, 0.30, 0.25, 0.20, 0.235)
+
+
+def cortical_columns(n_voxels: int, voxel_size: int, d_in: int = 1000, seed: int = 1, *,
+                     exc_frac: float = 0.8, d_within=(1, 20), d_cross=(20, 100),
+                     w_mu: float = -1.0, w_sigma: float = 0.5, density: float = 0.3,
+                     threads: int = 0) -> Graph:
+    """Micro-column network (Extended Data Table 3; Supplementary Sec. 2,
+    Eqs. 5-6): each voxel is a region of ten populations (E and I of layers
+    1, 2/3, 4, 5, 6; E populations first).  A neuron of population i gets
+    k_i * M[i][j] / sum_k M[i][k] synapses from population j of its voxel and
+    k_i * M[i][CC] / sum_k M[i][k] from excitatory neurons of other voxels
+    (source voxel by a seeded region matrix), where k_i is proportional to
+    the row sum of M and scaled so the mean in-degree is d_in (the table's
+    counts exceed the paper's in-degree cap of 1000).  Counts above a local
+    population's size are capped at it."""
+    layer_of = (0, 0, 1, 1, 2, 2, 3, 3, 4, 4)
+    exc = (1, 0) * 5
+    size = []
+    for p in range(10):
+        f = LAYER_FRACTION[layer_of[p]] * (exc_frac if exc[p] else 1.0 - exc_frac)
+        size.append(max(2, int(round(f * voxel_size))))
+    size[2] += voxel_size - sum(size)  # e2/3 absorbs the rounding
+    order = [p for p in range(10) if exc[p]] + [p for p in range(10) if not exc[p]]
+    M = np.array(COLUMN_TABLE, dtype=np.float64)
+    src_col = {name: c for c, name in enumerate(COLUMN_SOURCES)}
+    rows = M.sum(axis=1)
+    mean_row = sum(rows[p] * size[p] for p in range(10)) / voxel_size
+    K = rows * (d_in / mean_row)
+    P = 10
+    k_local = np.zeros((P, P), dtype=np.int32)
+    k_cc = np.zeros(P, dtype=np.int32)
+    pos = {p: i for i, p in enumerate(order)}
+    for ti, p in enumerate(order):
+        for si, q in enumerate(order):
+            name = COLUMN_POPS[q]
+            if name in src_col:
+                k_local[ti, si] = int(round(K[p] * M[p, src_col[name]] / rows[p]))
+        k_cc[ti] = int(round(K[p] * M[p, src_col["CC"]] / rows[p]))
+    offs = np.zeros(P + 1, dtype=np.int32)
+    offs[1:] = np.cumsum([size[p] for p in order])
+    n_exc_v = int(sum(size[p] for p in order if exc[p]))
+    V = int(n_voxels)
+    prob = region_matrix(V, density, seed + 7) if V > 1 else None
+    sp = _ColumnSpec(V, P, offs.ctypes.data, int(voxel_size), n_exc_v, k_local.ctypes.data,
+                     k_cc.ctypes.data, prob.ctypes.data if prob is not None else None,
+                     d_within[0], d_within[1], d_cross[0], d_cross[1], w_mu, w_sigma, seed)
+    N = V * int(voxel_size)
+    row_ptr = np.empty(N + 1, dtype=np.int64)
+    rc = lib().synth_columns(ctypes.byref(sp), row_ptr.ctypes.data, None, None, None, threads)
+    if rc != 0:
+        raise ValueError("synth_columns rejected the spec (code %d)" % rc)
+    E = int(row_ptr[-1])
+    col = np.empty(E, dtype=np.int32)
+    w = np.empty(E, dtype=np.uint16)
+    d = np.empty(E, dtype=np.uint8)
+    rc = lib().synth_columns(ctypes.byref(sp), row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data,
+                             d.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("synth_columns rejected the spec (code %d)" % rc)
+    ro = np.arange(V + 1, dtype=np.int32) * int(voxel_size)
+    n_exc = np.full(V, n_exc_v, dtype=np.int32)
+    g = Graph(N, V, ro, n_exc, row_ptr, col, w, d, max(d_within[1], d_cross[1] if V > 1 else 0))
+    g.populations = dict(order=[COLUMN_POPS[p] for p in order], offsets=offs, k_local=k_local,
+                         k_cc=k_cc)
+    return g
 
 
 def graph_from_dense(W: np.ndarray, Dl: np.ndarray, sizes, exc_frac: float = 0.8) -> Graph:

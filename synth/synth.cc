@@ -302,3 +302,196 @@ int synth_graph(const SynthSpec* spp, int64_t* row_ptr, int32_t* col,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Cortical micro-column networks (Extended Data Table 3; Supplementary
+// Sec. 2, Eqs. 5-6): every region (voxel) holds the same list of
+// populations; a neuron of population i receives exactly k_local[i][j]
+// synapses from population j of its own voxel (sources uniform without
+// replacement, no autapse) and k_cc[i] cortico-cortical synapses from
+// excitatory neurons of other voxels, the source voxel following the
+// row-stochastic region matrix (no multapse).
+extern "C" {
+
+struct ColumnSpec {
+  int32_t n_voxels, n_pops;
+  const int32_t* pop_offset;  // [n_pops + 1] offsets of the populations inside a voxel
+  int32_t voxel_size;         // neurons per voxel (= pop_offset[n_pops])
+  int32_t n_exc;              // excitatory neurons per voxel (populations come E first)
+  const int32_t* k_local;     // [n_pops][n_pops]
+  const int32_t* k_cc;        // [n_pops]
+  const double* region_prob;  // [V*V] row-stochastic, diagonal ignored
+  int32_t d_within_min, d_within_max, d_cross_min, d_cross_max;
+  double w_mu, w_sigma;
+  uint64_t seed;
+};
+
+}  // extern "C"
+
+namespace {
+
+struct ColumnSampler {
+  const ColumnSpec& sp;
+  const std::vector<std::vector<double>>& cdf;
+  std::vector<uint64_t> bitmap;
+  std::vector<int32_t> chosen, hset;
+  std::vector<size_t> used;
+
+  ColumnSampler(const ColumnSpec& s, const std::vector<std::vector<double>>& c) : sp(s), cdf(c) {
+    int32_t maxp = 1, maxcc = 1;
+    for (int32_t p = 0; p < s.n_pops; ++p) {
+      maxp = std::max(maxp, s.pop_offset[p + 1] - s.pop_offset[p]);
+      maxcc = std::max(maxcc, s.k_cc[p]);
+    }
+    bitmap.assign((size_t)maxp / 64 + 1, 0ull);
+    int hs = 16;
+    while (hs < 4 * (maxcc + 1)) hs <<= 1;
+    hset.assign((size_t)hs, -1);
+  }
+
+  template <class F>
+  void run(int32_t tgt, F&& emit) {
+    Rng g(sp.seed, 0xC01Full, (uint64_t)tgt);
+    const int32_t v = tgt / sp.voxel_size, local = tgt % sp.voxel_size;
+    int32_t pi = 0;
+    while (local >= sp.pop_offset[pi + 1]) ++pi;
+    const int32_t vbase = v * sp.voxel_size;
+    for (int32_t pj = 0; pj < sp.n_pops; ++pj) {
+      const int32_t a = sp.pop_offset[pj], n = sp.pop_offset[pj + 1] - a;
+      const bool same = pj == pi;
+      const int32_t m = n - (same ? 1 : 0);  // candidates (self excluded)
+      const int32_t k = std::min(sp.k_local[pi * sp.n_pops + pj], m);
+      if (k <= 0) continue;
+      const int32_t self = local - a;
+      chosen.clear();
+      for (int32_t j = m - k; j < m; ++j) {  // Floyd's sampling
+        int32_t t = (int32_t)g.below((uint32_t)j + 1);
+        int32_t pick = (bitmap[t >> 6] >> (t & 63)) & 1ull ? j : t;
+        bitmap[pick >> 6] |= 1ull << (pick & 63);
+        chosen.push_back(pick);
+      }
+      for (int32_t c : chosen) {
+        bitmap[c >> 6] &= ~(1ull << (c & 63));
+        const int32_t idx = same && c >= self ? c + 1 : c;
+        emit(vbase + a + idx, tgt, true);
+      }
+    }
+    const int32_t kc = sp.n_voxels > 1 ? sp.k_cc[pi] : 0;
+    if (kc <= 0 || sp.n_exc <= 0) return;
+    const size_t hmask = hset.size() - 1;
+    used.clear();
+    for (int32_t q = 0; q < kc; ++q) {
+      int32_t src;
+      for (;;) {
+        const std::vector<double>& row = cdf[(size_t)v];
+        int32_t vv = (int32_t)(std::lower_bound(row.begin(), row.end(), g.unit()) - row.begin());
+        if (vv >= sp.n_voxels) vv = sp.n_voxels - 1;
+        if (vv == v) continue;
+        src = vv * sp.voxel_size + (int32_t)g.below((uint32_t)sp.n_exc);
+        size_t h = ((uint64_t)src * 0x9E3779B97F4A7C15ull) >> 20;
+        bool dup = false;
+        for (;;) {
+          h &= hmask;
+          if (hset[h] == -1) break;
+          if (hset[h] == src) { dup = true; break; }
+          ++h;
+        }
+        if (dup) continue;
+        hset[h] = src;
+        used.push_back(h);
+        break;
+      }
+      emit(src, tgt, false);
+    }
+    for (size_t h : used) hset[h] = -1;
+  }
+
+  void attributes(int32_t src, int32_t tgt, bool within, uint8_t* d, uint16_t* w) const {
+    Rng g(sp.seed, 0xED6Eull ^ ((uint64_t)(uint32_t)src << 20), (uint64_t)tgt);
+    int32_t lo = within ? sp.d_within_min : sp.d_cross_min;
+    int32_t hi = within ? sp.d_within_max : sp.d_cross_max;
+    *d = (uint8_t)(lo + (int32_t)g.below((uint32_t)(hi - lo + 1)));
+    *w = f32_to_bf16_rne((float)std::exp(sp.w_mu + sp.w_sigma * g.normal()));
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Out-degrees first (row_ptr), then the CSR by source sorted by (delay,
+// target), as synth_graph.  Returns 0 or a negative code.
+int synth_columns(const ColumnSpec* spp, int64_t* row_ptr, int32_t* col, uint16_t* w_bf16,
+                  uint8_t* delay, int32_t nthreads) {
+  if (!spp || !row_ptr) return -1;
+  const ColumnSpec& sp = *spp;
+  const int32_t V = sp.n_voxels, P = sp.n_pops;
+  if (V < 1 || P < 1 || sp.voxel_size < 2 || sp.pop_offset[0] != 0 ||
+      sp.pop_offset[P] != sp.voxel_size || sp.n_exc < 0 || sp.n_exc > sp.voxel_size)
+    return -2;
+  if ((int64_t)V * sp.voxel_size >= (int64_t(1) << 31)) return -3;
+  if (sp.d_within_min < 1 || sp.d_within_max < sp.d_within_min || sp.d_within_max > 255 ||
+      sp.d_cross_min < 1 || sp.d_cross_max < sp.d_cross_min || sp.d_cross_max > 255)
+    return -6;
+  std::vector<std::vector<double>> cdf((size_t)V);
+  for (int32_t r = 0; r < V && V > 1; ++r) {
+    cdf[(size_t)r].resize((size_t)V);
+    double acc = 0.0, tot = 0.0;
+    for (int32_t c = 0; c < V; ++c) tot += c == r ? 0.0 : (sp.region_prob ? sp.region_prob[(int64_t)r * V + c] : 1.0);
+    if (tot <= 0.0) return -7;
+    for (int32_t c = 0; c < V; ++c) {
+      acc += (c == r ? 0.0 : (sp.region_prob ? sp.region_prob[(int64_t)r * V + c] : 1.0)) / tot;
+      cdf[(size_t)r][(size_t)c] = acc;
+    }
+    cdf[(size_t)r][(size_t)V - 1] = 1.0;
+  }
+  const int32_t N = V * sp.voxel_size;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  std::vector<std::atomic<int32_t>> outdeg((size_t)N);
+  for (auto& x : outdeg) x.store(0, std::memory_order_relaxed);
+#pragma omp parallel
+  {
+    ColumnSampler cs(sp, cdf);
+#pragma omp for schedule(dynamic, 256)
+    for (int32_t i = 0; i < N; ++i)
+      cs.run(i, [&](int32_t s, int32_t, bool) { outdeg[(size_t)s].fetch_add(1, std::memory_order_relaxed); });
+  }
+  row_ptr[0] = 0;
+  for (int32_t j = 0; j < N; ++j) row_ptr[j + 1] = row_ptr[j] + outdeg[(size_t)j].load();
+  if (!col) return 0;  // out-degrees only: the caller sizes the edge arrays
+  const int64_t E = row_ptr[N];
+  std::vector<uint64_t> key((size_t)E);
+  for (auto& x : outdeg) x.store(0, std::memory_order_relaxed);
+#pragma omp parallel
+  {
+    ColumnSampler cs(sp, cdf);
+#pragma omp for schedule(dynamic, 256)
+    for (int32_t i = 0; i < N; ++i)
+      cs.run(i, [&](int32_t s, int32_t t, bool within) {
+        uint8_t d;
+        uint16_t w;
+        cs.attributes(s, t, within, &d, &w);
+        int32_t p = outdeg[(size_t)s].fetch_add(1, std::memory_order_relaxed);
+        key[(size_t)(row_ptr[s] + p)] = ((uint64_t)d << 56) | ((uint64_t)(uint32_t)i << 16) | (uint64_t)w;
+      });
+  }
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int32_t j = 0; j < N; ++j) {
+    uint64_t* a = key.data() + row_ptr[j];
+    uint64_t* b = key.data() + row_ptr[j + 1];
+    std::sort(a, b);
+    for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+      uint64_t k = key[(size_t)e];
+      delay[e] = (uint8_t)(k >> 56);
+      col[e] = (int32_t)((k >> 16) & 0xFFFFFFFFull);
+      w_bf16[e] = (uint16_t)(k & 0xFFFFull);
+    }
+  }
+  return 0;
+}
+
+}  // extern "C"

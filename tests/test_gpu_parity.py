@@ -364,3 +364,20 @@ def test_heterogeneous_injected_current_bit_exact():
     assert len(ids) > 500
     assert np.array_equal(st, rs) and np.array_equal(ids, rids)
     _assert_same_state(net, o, "heterogeneous I_ext")
+
+
+def test_cortical_column_network_bit_exact():
+    """Micro-column network (Extended Data Table 3): ten populations per
+    voxel, heavy-tailed out-degree -- matched-FP32 bit-exact over 100 ms."""
+    g = synth.cortical_columns(4, 2500, 150, seed=17)
+    p = synth.scale_for_degree(synth.default_region_params(I_ext=0.95), 150)
+    net = _net(g, p, seed=19)
+    o = oracle.Sim(g, p, seed=19, precision=32)
+    net.step(1000)
+    o.step(1000)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 1000
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "columns")
+    assert net.stats()["events"] == _delivered_by(g, st, ids, 1000)

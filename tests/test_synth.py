@@ -65,3 +65,37 @@ def test_bf16_round_trip():
     y = synth.bf16_to_f64(b)
     assert np.all(np.abs(y - x) <= np.abs(x) * 2.0**-8)
     assert np.array_equal(synth.f64_to_bf16(y), b)
+
+
+def test_cortical_columns_follow_the_population_counts():
+    """Extended Data Table 3 networks: every neuron of population i gets
+    exactly the scaled count from each population of its voxel and from
+    excitatory neurons of other voxels; no autapse or multapse; the
+    out-degree is heavy-tailed (small layer-1 populations feed many)."""
+    V, n = 4, 2000
+    g = synth.cortical_columns(V, n, 200, seed=9)
+    pops = g.populations
+    offs, kl, kc = pops["offsets"], pops["k_local"], pops["k_cc"]
+    n_exc = int(g.n_exc[0])
+    rp = np.asarray(g.row_ptr)
+    src = np.repeat(np.arange(g.n_neurons), np.diff(rp))
+    tgt = np.asarray(g.col)
+    assert not np.any(src == tgt)
+    pair = tgt.astype(np.int64) * g.n_neurons + src
+    assert len(np.unique(pair)) == len(pair)
+    same = src // n == tgt // n
+    pop_of = np.searchsorted(offs, np.arange(n), side="right") - 1
+    tpop = pop_of[np.arange(g.n_neurons) % n]   # population of every neuron
+    # cortico-cortical sources: excitatory neurons of another voxel
+    assert np.all((src[~same] % n) < n_exc)
+    # local counts per (target, source population), capped at the source
+    # population's size (minus the target itself in its own population)
+    cnt = np.zeros((g.n_neurons, len(offs) - 1), dtype=np.int64)
+    np.add.at(cnt, (tgt[same], pop_of[src[same] % n]), 1)
+    sizes = np.diff(offs)
+    expect = np.minimum(kl[tpop], sizes[None, :] - np.eye(len(sizes), dtype=np.int64)[tpop])
+    assert np.array_equal(cnt, expect)
+    assert np.array_equal(np.bincount(tgt[~same], minlength=g.n_neurons), kc[tpop])
+    deg = np.diff(rp)
+    assert deg.max() > 3 * np.median(deg)
+    assert abs(len(tgt) / g.n_neurons - 200) < 10
