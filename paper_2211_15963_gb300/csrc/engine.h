@@ -106,8 +106,8 @@ struct alignas(16) InstDesc {
   const uint16_t* rec;           // interleaved records, or nullptr for col/w/delay
   const uint32_t* col;
   const uint16_t* w;
-  const uint8_t* delay;          // nullptr when the delay is packed into col
-  const void* seg;               // [N][dmax] segment table, or nullptr
+  const uint8_t* delay;          // col/w/delay: caller-held arrays (allocation-free runs)
+  const void* seg;               // [N][seg_stride] segment table, or nullptr
   const int32_t* region_offsets; // [R+1], local
   const RegionConst* rc;         // [R]
   double* bold;                  // [bold_cap][R]
@@ -119,7 +119,7 @@ struct alignas(16) InstDesc {
   uint64_t seed, net_id;
   unsigned long long g0;         // engine iteration at which this instance's step 0 ran
   long long n_end;               // steps it runs: later iterations leave it unchanged
-  int32_t N, R, rbase, shift;
+  int32_t N, R, rbase, shift;    // shift, tmask: the col/w/delay form (targets col & tmask)
   uint32_t tmask;
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;

@@ -4,15 +4,20 @@
 //              equation and Eq. 2; Supplementary Sec. 3, Eqs. 3 and 5 with
 //              the refractory reset), the Poisson background drawn from
 //              Philox4x64-10, spike compaction into the spike ring,
-//              and region spike counts.
+//              and region spike counts; k_update<true> also integrates the
+//              background OU current (Eq. 1) and applies the per-neuron
+//              injected-current factors.
 //   k_close / the head of k_deliver: the per-bin Balloon-Windkessel step
 //              (Extended Data Table 4) and the BOLD sample, one region per
 //              thread.
 //   k_deliver  push delivery (Supplementary Algorithm 2) at arrival time: for
 //              every spike of step n - d (d = 1..D-1, from the spike ring)
 //              the edges of its row with delay exactly d -- one contiguous
-//              segment found in the per-delay segment table -- are added to
-//              this step's fixed-point accumulators.
+//              segment, read from the delay-major segment ring that the
+//              leading blocks fill for the previous step's spikes (or from
+//              the graph's segment table) -- are added to this step's
+//              fixed-point accumulators, the warp's segments laid end to end
+//              so that consecutive lanes read consecutive edge records.
 //
 // Both kernels find their iteration through a StepRef (a base word in device
 // memory plus an offset), so a captured CUDA graph of (deliver, update) pairs
