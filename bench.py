@@ -440,9 +440,10 @@ def run_ensemble(args):
     # batched: every member in each launch, one analysis per TR
     ens = dbnet.Ensemble(g, base, M, theta, dict(opts, net_id=0), enkf, stream)
     err0 = float(np.abs(theta[:, :, 0].mean(0) - hidden_th[:, 0]).mean())
+    y_pred = []  # the forecast ensemble mean of every TR, before its analysis
     for k in range(args.warmup):
         ens.step(TR_STEPS)
-        ens.assimilate(y_obs[k])
+        y_pred.append(ens.assimilate(y_obs[k]))
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     s0 = ens.stats()
@@ -452,7 +453,7 @@ def run_ensemble(args):
         ev[k][0].record(stream)
         ens.step(TR_STEPS)
         ev[k][1].record(stream)
-        ens.assimilate(y_obs[args.warmup + k])   # reads the predicted mean back (synchronises)
+        y_pred.append(ens.assimilate(y_obs[args.warmup + k]))  # reads the forecast mean back
         ev[k][2].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -465,6 +466,15 @@ def run_ensemble(args):
     th_now, _, _ = ens.read()
     err1 = float(np.abs(th_now[:, :, 0].mean(0) - hidden_th[:, 0]).mean())
     ens.close()
+    # fit of the forecast BOLD to the hidden member's (per-region correlation
+    # over the TRs, and the relative error early and late)
+    yp, yo = np.array(y_pred), np.array(y_obs[:len(y_pred)])
+    pcc = [float(np.corrcoef(yp[:, r], yo[:, r])[0, 1]) for r in range(R) if yo[:, r].std() > 0]
+    rel = np.abs(yp - yo).mean(axis=1) / np.abs(yo).mean(axis=1)
+    q = max(1, len(rel) // 4)
+    bold_fit = {"pcc_mean_over_regions": float(np.mean(pcc)) if pcc else None,
+                "rel_err_first_quarter": float(rel[:q].mean()),
+                "rel_err_last_quarter": float(rel[-q:].mean()), "trs": int(len(rel))}
 
     # one network per launch: the same members as independent networks,
     # stepped one after another, each from its own captured graph
@@ -508,6 +518,7 @@ def run_ensemble(args):
         "mean_rate_hz": spikes / (M * g.n_neurons) / bio_s,
         "analysis_ms_per_tr": an_ms / args.steps, "simulate_ms_per_tr": sim_ms / args.steps,
         "theta_ampa_mean_abs_err": {"start": err0, "end": err1, "trs": n_tr},
+        "bold_fit": bold_fit,
         "separate": {"value": sep_value, "unit": UNIT, "ms_per_tr": sep_ms / args.separate_trs,
                      "what": "the same %d members as independent networks, one network's "
                              "kernels per launch, stepped one after another (simulation only, "

@@ -126,3 +126,33 @@ def test_shared_graph_key_and_failed_neighbour():
     with pytest.raises(dbnet.DbnetError):
         srv.poll(a)
     srv.close()
+
+
+def test_random_stream_through_a_tight_pool():
+    """Twelve random requests (sizes, regions, in-degrees, durations) arrive
+    at random rounds into a pool too small for all of them: they queue,
+    reuse tiles and region slots, and each still equals its run alone."""
+    from paper_2211_15963_gb300 import dbnet
+    rng = np.random.default_rng(123)
+    reqs = []
+    for i in range(12):
+        n = int(rng.integers(800, 4000))
+        R = int(rng.integers(1, 4))
+        k = int(rng.integers(30, 90))
+        g, p = _request(20 + i, n, R, k)
+        reqs.append((g, p, int(rng.integers(200, 1500)), 100 + i, 50 + i, int(rng.integers(0, 12))))
+    srv = dbnet.Server(max_neurons=8192, max_requests=3, max_regions=8, max_delay=60,
+                       chunk_steps=64, arena_bytes=256 << 20, run=RUN)
+    ids = {}
+    for rnd in range(400):
+        for i, r in enumerate(reqs):
+            if r[5] == rnd:
+                ids[i] = srv.submit(r[0], r[1], r[2], seed=r[3], net_id=r[4],
+                                    raster_capacity=1 << 20)
+        srv.pump()
+        if len(ids) == len(reqs) and all(srv.poll(v)["state"] == 2 for v in ids.values()):
+            break
+    srv.drain()
+    for i, (g, p, n, seed, nid, _) in enumerate(reqs):
+        _check(srv, ids[i], _alone(g, p, n, seed, nid))
+    srv.close()
