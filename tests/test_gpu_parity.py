@@ -381,3 +381,27 @@ def test_cortical_column_network_bit_exact():
     assert np.array_equal(st, rs) and np.array_equal(ids, rids)
     _assert_same_state(net, o, "columns")
     assert net.stats()["events"] == _delivered_by(g, st, ids, 1000)
+
+
+def test_lowered_fixed_point_scale_bit_exact():
+    """Large weights: in-degree x q(w_max) would overflow int32 at S = 16, so
+    both sides lower S by the same rule and stay bit-exact; an explicit S
+    that could overflow is refused (DBNET_EOVERFLOW)."""
+    from paper_2211_15963_gb300 import dbnet
+    g = synth.make_graph([2000, 1000], 200, 71, w_mu=4.0, w_sigma=0.5, d_within=(1, 15),
+                         d_cross=(15, 40))
+    p = synth.default_region_params()
+    net = _net(g, p, seed=3)
+    o = oracle.Sim(g, p, seed=3, precision=32)
+    assert net.stats()["fixed_shift"] == o.info()["S"] < 16
+    net.step(300)
+    o.step(300)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 100
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "lowered S")
+    net.close()
+    with pytest.raises(dbnet.DbnetError) as ei:
+        dbnet.Network(g, p, dict(fixed_shift=20))
+    assert ei.value.code == dbnet.DBNET_EOVERFLOW
