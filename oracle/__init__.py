@@ -53,7 +53,8 @@ class OgGraph(ctypes.Structure):
     _fields_ = [("n_neurons", ctypes.c_int32), ("n_regions", ctypes.c_int32),
                 ("region_offsets", ctypes.c_void_p), ("n_exc", ctypes.c_void_p),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
-                ("w_bf16", ctypes.c_void_p), ("delay", ctypes.c_void_p)]
+                ("w_bf16", ctypes.c_void_p), ("delay", ctypes.c_void_p),
+                ("w2_bf16", ctypes.c_void_p)]
 
 
 class OgRegion(ctypes.Structure):
@@ -179,9 +180,11 @@ class Sim:
         assert len(region_params) == graph.n_regions
         self.graph = graph  # keep the arrays alive
         self._regs = (OgRegion * graph.n_regions)(*[region_struct(p) for p in region_params])
+        w2 = getattr(graph, "w2_bf16", None)
+        w2 = _addr(w2) if w2 is not None else None
         g = OgGraph(graph.n_neurons, graph.n_regions, _addr(graph.region_offsets),
                     _addr(graph.n_exc), _addr(graph.row_ptr), _addr(graph.col),
-                    _addr(graph.w_bf16), _addr(graph.delay))
+                    _addr(graph.w_bf16), _addr(graph.delay), w2)
         o = OgOptions(dt_ms, bin_ms, tr_ms, z_scale, bw["kappa"], bw["gamma"], bw["tau"],
                       bw["alpha"], bw["rho"], bw["V0"], seed, net_id, fixed_shift, precision)
         err = ctypes.c_int(0)
@@ -259,8 +262,11 @@ class Sim:
         return x
 
     def ring(self) -> np.ndarray:
+        """[D][N][channels]: the 2 classes (E, I), or with two weights per
+        edge the 4 channels (AMPA, NMDA, GABA_A, GABA_B)."""
         D = self.info()["D"]
-        r = np.zeros((D, self.N, 2), dtype=np.int64)
+        nch = 4 if getattr(self.graph, "w2_bf16", None) is not None else 2
+        r = np.zeros((D, self.N, nch), dtype=np.int64)
         lib().og_read_ring(self._h, r.ctypes.data)
         return r
 

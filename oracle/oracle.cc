@@ -29,6 +29,12 @@
 //     the accumulator read at step n+d (d = 1 is Eq. 3's one-step latency).
 //   * One weight per edge, shared by both channels of the source's class, so
 //     the accumulator has two classes: E (AMPA, NMDA) and I (GABA_A, GABA_B).
+//     Optionally a second weight per edge, as the connection table of
+//     Supplementary Table 5 stores one weight per channel: the first feeds
+//     AMPA (excitatory source) or GABA_A (inhibitory), the second NMDA or
+//     GABA_B, and the accumulator has the four channels.  The background
+//     drive then adds w_ext to both AMPA and NMDA, as it adds to E in the
+//     one-weight form.
 //   * Accumulators hold fixed point: q(w) = rint(w * 2^S).
 //   * Background: K_ext independent Poisson sources of rate nu per neuron,
 //     each adding w_ext to the E class; the count per step is drawn by integer
@@ -113,6 +119,7 @@ struct OgGraph {
   const int32_t* col;             // [E] target
   const uint16_t* w_bf16;         // [E]
   const uint8_t* delay;           // [E] steps >= 1
+  const uint16_t* w2_bf16;        // [E] second channel's weight, or NULL (one weight)
 };
 
 struct OgRegion {  // units: mV, ms, nF, uS, nA
@@ -233,8 +240,9 @@ struct SimBase {
   virtual void set_ibg(const double* I) = 0;
   // shared bookkeeping
   int32_t N = 0, R = 0, D = 0, S = 0, spb = 0, bins_per_tr = 0;
+  int32_t nch = 2;  // accumulator channels: 2 classes, or 4 with two weights per edge
   int64_t n = 0, events = 0, spikes = 0, bins_done = 0;
-  std::vector<int64_t> ring;  // [D][N][2]
+  std::vector<int64_t> ring;  // [D][N][nch]
   std::vector<int32_t> raster_step, raster_id;
   std::vector<int32_t> region_of, cnt;
   std::vector<double> bw;    // [R][4]
@@ -258,13 +266,20 @@ struct Sim : SimBase {
   }
 
   // Supplementary Algorithm 2, the push of a spike's synaptic input: every
-  // out-edge of spiker j adds q(w) to the accumulator slot its delay selects.
+  // out-edge of spiker j adds q(w) to the accumulator slot its delay selects
+  // (with two weights: q(w) to channel 2c and q(w2) to channel 2c + 1).
   void scatter(int32_t j, int64_t step_n) {
     int32_t c = class_of(j);
     for (int64_t e = g.row_ptr[j]; e < g.row_ptr[j + 1]; ++e) {
       int64_t slot = (step_n + g.delay[e]) % D;
       int64_t q = (int64_t)std::lrint(std::ldexp(bf16_value(g.w_bf16[e]), S));
-      ring[(size_t)((slot * N + g.col[e]) * 2 + c)] += q;
+      if (nch == 2) {
+        ring[(size_t)((slot * N + g.col[e]) * 2 + c)] += q;
+      } else {
+        int64_t q2 = (int64_t)std::lrint(std::ldexp(bf16_value(g.w2_bf16[e]), S));
+        ring[(size_t)((slot * N + g.col[e]) * 4 + 2 * c)] += q;
+        ring[(size_t)((slot * N + g.col[e]) * 4 + 2 * c + 1)] += q2;
+      }
       ++events;
     }
   }
@@ -280,15 +295,18 @@ struct Sim : SimBase {
       std::vector<int32_t> fired;
       for (int32_t i = 0; i < N; ++i) {
         const RegionConst<Real>& p = rc[(size_t)region_of[(size_t)i]];
-        int64_t* a = &ring[(size_t)((slot * N + i) * 2)];
-        int64_t aE = a[0], aI = a[1];
-        a[0] = 0;
-        a[1] = 0;
+        // this step's arrivals per channel (AMPA, NMDA, GABA_A, GABA_B): in
+        // the one-weight form both channels of a class read its class sum
+        int64_t* a = &ring[(size_t)((slot * N + i) * nch)];
+        int64_t ach[4];
+        for (int u4 = 0; u4 < 4; ++u4) ach[u4] = nch == 2 ? a[u4 / 2] : a[u4];
+        for (int k = 0; k < nch; ++k) a[k] = 0;
         // background Poisson count by integer inversion
         uint32_t u = (uint32_t)(neuron_word(o.seed, o.net_id, (uint64_t)n, i, 0) >> 32);
         int64_t c = 0;
         for (int32_t k = 0; k < p.n_thr; ++k) c += (u >= p.thr[k]) ? 1 : 0;
-        aE += c * (int64_t)p.q_ext;
+        ach[0] += c * (int64_t)p.q_ext;
+        ach[1] += c * (int64_t)p.q_ext;
         // membrane (Eq. 5, bracket times dt/C) with the old V and J
         Real v = V[(size_t)i];
         Real Isyn = (Real)0;
@@ -320,12 +338,11 @@ struct Sim : SimBase {
           ib = ib + t2;
         }
         // synaptic traces (Eq. 3): decay, then this step's arrivals
-        Real xE = (Real)aE * inv2S;
-        Real xI = (Real)aI * inv2S;
         for (int u4 = 0; u4 < 4; ++u4) {
+          Real x = (Real)ach[u4] * inv2S;
           Real& j = J[(size_t)u4 * N + i];
           Real d = p.dec[u4] * j;
-          j = d + (u4 < 2 ? xE : xI);
+          j = d + x;
         }
         // refractory clamp, threshold and reset
         if (ref[(size_t)i] > 0) {
@@ -403,6 +420,10 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
     dmax = g->delay[e] > dmax ? g->delay[e] : dmax;
     double w = bf16_value(g->w_bf16[e]);
     wmax = w > wmax ? w : wmax;
+    if (g->w2_bf16) {
+      double w2 = bf16_value(g->w2_bf16[e]);
+      wmax = w2 > wmax ? w2 : wmax;
+    }
     indeg[(size_t)g->col[e]] += 1;
   }
   for (int32_t i = 0; i < N; ++i) kin_max = indeg[(size_t)i] > kin_max ? indeg[(size_t)i] : kin_max;
@@ -476,7 +497,8 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
     Real t = span * u;
     s->V[(size_t)i] = p.Vreset + t;
   }
-  s->ring.assign((size_t)s->D * N * 2, 0);
+  s->nch = g->w2_bf16 ? 4 : 2;
+  s->ring.assign((size_t)s->D * N * s->nch, 0);
   s->cnt.assign((size_t)R, 0);
   s->bw.resize((size_t)R * 4);
   for (int32_t r = 0; r < R; ++r) {

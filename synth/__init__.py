@@ -115,6 +115,7 @@ class Graph:
     w_bf16: object              # uint16 [E] (BF16 bit patterns)
     delay: object               # uint8 [E], steps, >= 1
     max_delay: int
+    w2_bf16: object = None      # uint16 [E] second channel's weight, or None
 
     @property
     def n_edges(self) -> int:
@@ -272,28 +273,46 @@ def cortical_columns(n_voxels: int, voxel_size: int, d_in: int = 1000, seed: int
     return g
 
 
-def graph_from_dense(W: np.ndarray, Dl: np.ndarray, sizes, exc_frac: float = 0.8) -> Graph:
+def graph_from_dense(W: np.ndarray, Dl: np.ndarray, sizes, exc_frac: float = 0.8,
+                     W2: np.ndarray | None = None) -> Graph:
     """Build a Graph from dense matrices W[target, source] (0 = no edge, values
     already representable in BF16) and Dl[target, source] (delays in steps).
-    Used for brute-force checks on tiny networks."""
+    With W2, every edge also carries a second weight (an edge exists where W
+    or W2 is non-zero).  Used for brute-force checks on tiny networks."""
     N = W.shape[0]
     ro, n_exc = region_layout(sizes, exc_frac)
     assert int(ro[-1]) == N
-    rows, cols, ws, ds = [], [], [], []
+    cols, ws, w2s, ds = [], [], [], []
     row_ptr = np.zeros(N + 1, dtype=np.int64)
+    mask = W != 0 if W2 is None else (W != 0) | (W2 != 0)
     for j in range(N):
-        tg = np.nonzero(W[:, j])[0]
+        tg = np.nonzero(mask[:, j])[0]
         order = np.lexsort((tg, Dl[tg, j]))
         tg = tg[order]
         cols.append(tg.astype(np.int32))
         ws.append(f64_to_bf16(W[tg, j]))
+        if W2 is not None:
+            w2s.append(f64_to_bf16(W2[tg, j]))
         ds.append(Dl[tg, j].astype(np.uint8))
         row_ptr[j + 1] = row_ptr[j] + len(tg)
     col = np.concatenate(cols) if cols else np.zeros(0, np.int32)
     w = np.concatenate(ws) if ws else np.zeros(0, np.uint16)
     d = np.concatenate(ds) if ds else np.zeros(0, np.uint8)
+    w2 = None
+    if W2 is not None:
+        w2 = np.concatenate(w2s) if w2s else np.zeros(0, np.uint16)
     dmax = int(d.max()) if len(d) else 1
-    return Graph(N, len(sizes), ro, n_exc, row_ptr, col, w, d, dmax)
+    return Graph(N, len(sizes), ro, n_exc, row_ptr, col, w, d, dmax, w2)
+
+
+def with_second_weight(g: Graph, seed: int, w_mu: float = -1.0, w_sigma: float = 0.5) -> Graph:
+    """The same graph with a second weight on every edge, drawn independently
+    from the lognormal(w_mu, w_sigma) of the first and rounded to BF16 (the
+    connection table of Supplementary Table 5 stores one weight per channel,
+    the channels' weights sharing a distribution)."""
+    rng = np.random.default_rng(seed)
+    w2 = f64_to_bf16(rng.lognormal(w_mu, w_sigma, g.n_edges))
+    return dataclasses.replace(g, w2_bf16=w2)
 
 
 # ---------------------------------------------------------------------------

@@ -204,6 +204,116 @@ def test_delivery_matches_brute_force_all_pairs(seed):
     assert s.info()["events"] == total
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_two_weight_delivery_matches_brute_force_all_pairs(seed):
+    """Supp. Algorithm 2 with the two weights per edge of Supp. Table 5,
+    against dense all-pairs sums: channel 2c + 0 of target i gets
+    sum over spiking j of class c of q(W_ij), channel 2c + 1 sum of q(W2_ij).
+    Some edges carry only one of the two weights."""
+    rng = np.random.default_rng(seed)
+    sizes = [50, 30]
+    N = sum(sizes)
+    E = rng.random((N, N)) < 0.3
+    W = np.where(E & (rng.random((N, N)) < 0.9), np.exp(rng.normal(-1, 0.5, (N, N))), 0.0)
+    W2 = np.where(E & (rng.random((N, N)) < 0.9), np.exp(rng.normal(-1, 0.5, (N, N))), 0.0)
+    np.fill_diagonal(W, 0.0)
+    np.fill_diagonal(W2, 0.0)
+    W = synth.bf16_to_f64(synth.f64_to_bf16(W))
+    W2 = synth.bf16_to_f64(synth.f64_to_bf16(W2))
+    Dl = rng.integers(1, 8, (N, N))
+    g = synth.graph_from_dense(W, Dl, sizes, W2=W2)
+    s = oracle.Sim(g, synth.default_region_params(drive_rate_hz=0.0), precision=32)
+    D, S = s.info()["D"], s.info()["S"]
+    exc = np.zeros(N, dtype=bool)
+    for r in range(len(sizes)):
+        exc[g.region_offsets[r]:g.region_offsets[r] + g.n_exc[r]] = True
+    expect = np.zeros((D, N, 4), dtype=np.int64)
+    total = 0
+    for call in range(4):
+        n = int(rng.integers(0, 50))
+        ids = np.sort(rng.choice(N, size=int(rng.integers(1, 20)), replace=False)).astype(np.int32)
+        s.deliver_only(ids, n)
+        for i in range(N):
+            for j in ids:
+                if W[i, j] != 0.0 or W2[i, j] != 0.0:
+                    c = 0 if exc[j] else 2
+                    slot = (n + Dl[i, j]) % D
+                    expect[slot, i, c] += int(np.rint(W[i, j] * 2.0**S))
+                    expect[slot, i, c + 1] += int(np.rint(W2[i, j] * 2.0**S))
+                    total += 1
+    assert np.array_equal(s.ring(), expect)
+    assert s.info()["events"] == total
+
+
+@pytest.mark.parametrize("exc_frac,channels", [(1.0, (0, 1)), (0.0, (2, 3))])
+def test_two_weight_traces_take_their_own_weight(exc_frac, channels):
+    """Supp. Eq. 3 per channel with two weights per edge: a spike of neuron 0
+    at step 0 over an edge of delay 3 with weights (0.75, 0.3125) reaches
+    neuron 1's first channel of the source's class with 0.75 and its second
+    with 0.3125; afterwards each decays with its own exp(-dt/tau_u)."""
+    W = np.zeros((2, 2))
+    W2 = np.zeros((2, 2))
+    W[1, 0], W2[1, 0] = 0.75, 0.3125
+    g = synth.graph_from_dense(W, np.full((2, 2), 3), [2], exc_frac, W2=W2)
+    p = synth.default_region_params(I_ext=0.0, drive_rate_hz=0.0)
+    s = oracle.Sim(g, p, precision=64)
+    s.set_state(V=np.array([-49.0, -70.0]), J=np.zeros((4, 2)), ref=np.zeros(2, np.int32))
+    traj = []
+    for _ in range(100):
+        s.step(1)
+        traj.append(s.state()[1][:, 1].copy())
+    traj = np.array(traj)
+    assert np.all(traj[:3] == 0.0)
+    other = [u for u in range(4) if u not in channels]
+    assert np.all(traj[:, other] == 0.0)
+    for u, w in zip(channels, (0.75, 0.3125)):
+        dec = math.exp(-0.1 / p["tau_u"][u])
+        assert np.allclose(traj[3:, u], w * dec ** np.arange(97), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_two_equal_weights_reduce_to_the_one_weight_form(small_graph, precision):
+    """With the second weight equal to the first on every edge, the four
+    channels receive what the two classes do in the one-weight form (the
+    background drive included): raster and state are identical."""
+    import dataclasses
+    g2 = dataclasses.replace(small_graph, w2_bf16=np.array(small_graph.w_bf16).copy())
+    p = synth.default_region_params()
+    a = oracle.Sim(small_graph, p, seed=9, precision=precision)
+    b = oracle.Sim(g2, p, seed=9, precision=precision)
+    a.step(400)
+    b.step(400)
+    assert a.info()["spikes"] > 50
+    for x, y in zip(a.raster(), b.raster()):
+        assert np.array_equal(x, y)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    assert a.info()["S"] == b.info()["S"]
+
+
+def test_two_weights_drive_feeds_both_excitatory_channels():
+    """The Poisson background (Ext. Data Table 2) with two weights per edge
+    and no recurrent edges: AMPA and NMDA traces follow the same arrivals,
+    each decaying with its own constant; GABA traces stay 0."""
+    W = np.zeros((4, 4))
+    g = synth.graph_from_dense(W, np.ones((4, 4), int), [4], 1.0, W2=W)
+    p = synth.default_region_params(I_ext=0.0, drive_rate_hz=2000.0, drive_K=1.0, w_ext=0.5)
+    s = oracle.Sim(g, p, seed=5, precision=64)
+    deA, deN = (math.exp(-0.1 / p["tau_u"][u]) for u in (0, 1))
+    prev = np.zeros((4, 4))
+    arrivals = 0
+    for _ in range(300):
+        s.step(1)
+        J = s.state()[1]
+        xA = J[0] - deA * prev[0]
+        xN = J[1] - deN * prev[1]
+        assert np.allclose(xA, xN, atol=1e-12)
+        arrivals += int(np.count_nonzero(xA > 0.25))
+        assert np.all(J[2:] == 0.0)
+        prev = J.copy()
+    assert arrivals > 120
+
+
 def test_events_equal_spikes_times_out_degree(small_graph):
     """Every spike delivers exactly its out-degree (Supp. Algorithm 2)."""
     s = oracle.Sim(small_graph, synth.default_region_params(), seed=15964, precision=32)
