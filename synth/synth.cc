@@ -268,8 +268,8 @@ int synth_graph(const SynthSpec* spp, int64_t* row_ptr, int32_t* col,
   row_ptr[0] = 0;
   for (int32_t j = 0; j < N; ++j) row_ptr[j + 1] = row_ptr[j] + outdeg[(size_t)j].load();
   const int64_t E = row_ptr[N];
-  // pass 2: the same draws again, scattered into rows as packed sort keys
-  std::vector<uint64_t> key((size_t)E);
+  // pass 2: the same draws again, scattered into the output rows (in
+  // arrival order); no memory beyond the output itself
   for (auto& x : outdeg) x.store(0, std::memory_order_relaxed);
 #pragma omp parallel
   {
@@ -280,22 +280,31 @@ int synth_graph(const SynthSpec* spp, int64_t* row_ptr, int32_t* col,
         uint8_t d;
         uint16_t w;
         ts.attributes(s, t, within, &d, &w);
-        int32_t p = outdeg[(size_t)s].fetch_add(1, std::memory_order_relaxed);
-        key[(size_t)(row_ptr[s] + p)] =
-            ((uint64_t)d << 56) | ((uint64_t)(uint32_t)i << 16) | (uint64_t)w;
+        const int64_t e = row_ptr[s] + outdeg[(size_t)s].fetch_add(1, std::memory_order_relaxed);
+        col[e] = i;
+        w_bf16[e] = w;
+        delay[e] = d;
       });
   }
-  // pass 3: sort each row by (delay, target) and unpack
-#pragma omp parallel for schedule(dynamic, 1024)
-  for (int32_t j = 0; j < N; ++j) {
-    uint64_t* a = key.data() + row_ptr[j];
-    uint64_t* b = key.data() + row_ptr[j + 1];
-    std::sort(a, b);
-    for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
-      uint64_t k = key[(size_t)e];
-      delay[e] = (uint8_t)(k >> 56);
-      col[e] = (int32_t)((k >> 16) & 0xFFFFFFFFull);
-      w_bf16[e] = (uint16_t)(k & 0xFFFFull);
+  // pass 3: sort each row by (delay, target) through a per-thread buffer of
+  // packed keys (one row at a time)
+#pragma omp parallel
+  {
+    std::vector<uint64_t> key;
+#pragma omp for schedule(dynamic, 1024)
+    for (int32_t j = 0; j < N; ++j) {
+      const int64_t a = row_ptr[j], n = row_ptr[j + 1] - a;
+      key.resize((size_t)n);
+      for (int64_t p = 0; p < n; ++p)
+        key[(size_t)p] = ((uint64_t)delay[a + p] << 56) | ((uint64_t)(uint32_t)col[a + p] << 16) |
+                         (uint64_t)w_bf16[a + p];
+      std::sort(key.begin(), key.end());
+      for (int64_t p = 0; p < n; ++p) {
+        const uint64_t k = key[(size_t)p];
+        delay[a + p] = (uint8_t)(k >> 56);
+        col[a + p] = (int32_t)((k >> 16) & 0xFFFFFFFFull);
+        w_bf16[a + p] = (uint16_t)(k & 0xFFFFull);
+      }
     }
   }
   return 0;
