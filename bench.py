@@ -43,6 +43,10 @@ STEPS_PER_BIO_S = 10_000  # dt = 0.1 ms
 RATE_DRIVE = {7: 3.1757, 15: 7.2221, 30: 16.4246}
 UPDATE_BYTES_PER_NEURON = 58   # V r/w 8, J r/w 32, ref r/w 2, accumulator read + clear 16
 DELIVER_BYTES_PER_EVENT = 14   # target|delay 4 + BF16 weight 2 + int32 read-modify-write 8
+# with two weights per edge: four accumulator channels (read + clear 32) and
+# 8-byte records (target 4 + two BF16 weights 4) with an int64 read-modify-write 16
+UPDATE_BYTES_PER_NEURON_FOUR = 74
+DELIVER_BYTES_PER_EVENT_TWO = 24
 METRIC = "synaptic events/s"
 UNIT = "events/s"
 
@@ -61,10 +65,16 @@ def parse_from(argv):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--profile-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--regions", type=int, default=100, help="regions of 20,000 neurons")
+    ap.add_argument("--regions", type=int, default=100, help="regions of --region-size neurons")
+    ap.add_argument("--region-size", type=int, default=20000,
+                    help="neurons per region (the largest configuration: 200 x 100,000)")
+    ap.add_argument("--pageable", action="store_true",
+                    help="host graph in pageable memory (for graphs too large to pin)")
     ap.add_argument("--k-in", type=int, default=1000, help="in-degree (80 %% within region)")
+    ap.add_argument("--two-weights", action="store_true",
+                    help="mid workload with a second weight per edge (four accumulator channels)")
     ap.add_argument("--workload", default="mid",
-                    choices=["mid", "ensemble", "serving", "nest", "columns"],
+                    choices=["mid", "ensemble", "serving", "nest", "columns", "dt-study"],
                     help="mid: the headline line; ensemble: 64-member HMDA ensemble (steps = "
                          "TRs) against one network per launch; serving: request stream")
     ap.add_argument("--members", type=int, default=64)
@@ -79,10 +89,14 @@ def parse_from(argv):
 
 
 def workload_config(args, rank_count):
-    return {"workload": "mid-size network: %d neurons, %d regions x 20,000, in-degree %d, "
-                        "dt 0.1 ms, ~%d Hz" % (args.regions * 20000, args.regions, args.k_in,
-                                                args.rate),
-            "neurons": args.regions * 20000, "regions": args.regions, "in_degree": args.k_in,
+    two = getattr(args, "two_weights", False)
+    rs = getattr(args, "region_size", 20000)
+    return {"workload": "%s network: %d neurons, %d regions x %d, in-degree %d, "
+                        "dt 0.1 ms, ~%d Hz%s" % ("mid-size" if args.regions * rs <= 2_000_000 else "large",
+                                                  args.regions * rs, args.regions, rs, args.k_in,
+                                                  args.rate, ", two weights per edge" if two else ""),
+            "weights_per_edge": 2 if two else 1,
+            "neurons": args.regions * rs, "regions": args.regions, "in_degree": args.k_in,
             "dt_ms": 0.1, "target_rate_hz": args.rate, "step": "1 biological second",
             "replicas": rank_count,
             "l2": "flushed (256 MiB write) between timed steps; edge arrays exceed L2"}
@@ -166,14 +180,14 @@ def kernels_sha():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, summary="traffic_mid_network.md"):
     """DRAM bytes per launch of `kernel` (ncu dram__bytes_read.sum +
-    dram__bytes_write.sum) from the committed summary
-    profiles/traffic_mid_network.md, when it was taken on the current kernel
+    dram__bytes_write.sum) from a committed summary under profiles/ (the
+    mid-size network's by default), when it was taken on the current kernel
     source: its line `kernels.cu sha256[:16]: <sha>` must match, and its
     table rows read `| <kernel> | <bytes per launch> | ...`."""
     import re
-    p = os.path.join(ROOT, "profiles", "traffic_mid_network.md")
+    p = os.path.join(ROOT, "profiles", summary)
     try:
         txt = open(p).read()
     except OSError:
@@ -254,11 +268,14 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)  # the library and every event use this stream
 
-    alloc, keep = pinned_alloc(torch)
+    alloc, keep = (None, None) if args.pageable else pinned_alloc(torch)
     seed = rank_seed(rank)
     t_gen = time.perf_counter()
-    g = synth.make_graph([20000] * args.regions, args.k_in, seed, k_within=int(round(0.8 * args.k_in)),
+    g = synth.make_graph([args.region_size] * args.regions, args.k_in, seed,
+                         k_within=int(round(0.8 * args.k_in)),
                          d_within=(1, 50), d_cross=(50, 200), alloc=alloc)
+    if args.two_weights:
+        g = synth.with_second_weight(g, seed + 5, alloc=alloc)
     t_gen = time.perf_counter() - t_gen
     params = params_for(args.rate, args.k_in)
     opts = dict(seed=seed + 1, net_id=rank)
@@ -304,16 +321,18 @@ def run_ours(args):
     n_prof = args.profile_steps
     ev_per_launch = (p1["events"] - p0["events"]) / n_prof
     hbm, peak_kind = peaks()
-    upd_bytes = g.n_neurons * UPDATE_BYTES_PER_NEURON
-    del_bytes = ev_per_launch * DELIVER_BYTES_PER_EVENT
+    two = args.two_weights
+    upd_bytes = g.n_neurons * (UPDATE_BYTES_PER_NEURON_FOUR if two else UPDATE_BYTES_PER_NEURON)
+    del_bytes = ev_per_launch * (DELIVER_BYTES_PER_EVENT_TWO if two else DELIVER_BYTES_PER_EVENT)
+    summary = "traffic_mid_network_two_weights.md" if two else "traffic_mid_network.md"
     kern = {
         "k_update": {"avg_us": 1e3 * t_upd / n_prof, "algorithmic_bytes": upd_bytes,
                      "achieved_gbs": upd_bytes / (t_upd / n_prof * 1e-3) / 1e9,
-                     "traffic": measured_traffic("k_update")},
+                     "traffic": measured_traffic("k_update", summary)},
         "k_deliver": {"avg_us": 1e3 * t_del / n_prof, "algorithmic_bytes": del_bytes,
                       "events_per_launch": ev_per_launch,
                       "achieved_gbs": del_bytes / (t_del / n_prof * 1e-3) / 1e9,
-                      "traffic": measured_traffic("k_deliver")},
+                      "traffic": measured_traffic("k_deliver", summary)},
     }
     dom = "k_update" if t_upd >= t_del else "k_deliver"
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": hbm,
@@ -325,7 +344,7 @@ def run_ours(args):
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
-        h2d = (g.row_ptr.nbytes + 4 * g.n_edges + 2 * g.n_edges + g.n_edges +
+        h2d = (g.row_ptr.nbytes + 4 * g.n_edges + (4 if two else 2) * g.n_edges + g.n_edges +
                g.region_offsets.nbytes + g.n_exc.nbytes + 200 * g.n_regions)
         d2h = 8 * g.n_regions + 96
         torch.cuda.synchronize()
@@ -348,7 +367,8 @@ def run_ours(args):
             dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
         e2e = {"value": float(ev_t.item()) / float(t_e2e.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "what": "dbnet_create from pinned host graph + 1 biological second + stats and "
+               "what": "dbnet_create from " + ("pageable" if args.pageable else "pinned") +
+                       " host graph + 1 biological second + stats and "
                        "BOLD read + destroy, per step (includes the onset transient)",
                "steps": args.e2e_steps, "bold_samples": int(len(y))}
 
@@ -767,6 +787,109 @@ def run_nest(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------- step-size accuracy study ----
+DT_STUDY_MS = (1.0, 0.5, 0.2, 0.1, 0.05, 0.02, 0.01, 0.008)   # the last is the reference
+DT_STUDY_STEPS = 1000   # 1 ms samples of V: one biological second
+
+
+def dt_study_network(dt_ms, seed):
+    """The 1,000-neuron network of the step-size study: one region, in-degree
+    100, every delay 1 ms (1/dt steps), the 1 ms-step conductances of the
+    NEST-comparison workload and a constant injected current with no random
+    drive, so that runs at different steps differ only by the Euler step."""
+    import dataclasses
+    import numpy as np
+    import synth
+    g = synth.make_graph([1000], 100, seed, d_within=(1, 1))
+    d = int(round(1.0 / dt_ms))
+    g = dataclasses.replace(g, delay=(np.asarray(g.delay, dtype=np.int64) * d).astype(np.uint8),
+                            max_delay=d)
+    p = synth.default_region_params(I_ext=NEST_DRIVE[12.1], drive_rate_hz=0.0)
+    p["g_u"] = tuple(x * NEST_G_SCALE for x in p["g_u"])
+    return g, p, d
+
+
+def matched_spikes(ref_t, ref_i, t, i, tol):
+    """Reference spikes (times ref_t of neurons ref_i) that have a spike of the
+    same neuron in (t, i) within tol."""
+    import numpy as np
+    hit = 0
+    for n in np.unique(ref_i):
+        a = ref_t[ref_i == n]
+        b = np.sort(t[i == n])
+        if len(b) == 0:
+            continue
+        k = np.searchsorted(b, a)
+        lo = b[np.clip(k - 1, 0, len(b) - 1)]
+        hi = b[np.clip(k, 0, len(b) - 1)]
+        hit += int((np.minimum(np.abs(a - lo), np.abs(hi - a)) <= tol).sum())
+    return hit
+
+
+def run_dt_study(args):
+    """Extended Data Fig. 1: membrane potentials of a 1,000-neuron LIF network
+    integrated by forward Euler at several steps, against the finest step
+    the device's 8-bit refractory counters allow (Tref = 2 ms in 250 steps).
+    V of every neuron is sampled every millisecond for one second; the
+    initial V (Philox counter of step 0) is the same at every step."""
+    import numpy as np
+    import torch
+    import synth
+    import __graft_entry__
+    from paper_2211_15963_gb300 import dbnet
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    seed = synth.seed_for(7)
+    runs = {}
+    for dt in DT_STUDY_MS:
+        g, p, d = dt_study_network(dt, seed)
+        net = dbnet.Network(g, p, dict(dt_ms=dt, bin_ms=1.0, seed=seed + 1,
+                                       raster_capacity=1 << 22), stream)
+        V = np.empty((DT_STUDY_STEPS, g.n_neurons), dtype=np.float64)
+        t0 = time.perf_counter()
+        for ms in range(DT_STUDY_STEPS):
+            net.step(d)
+            V[ms] = net.state()[0]
+        wall = time.perf_counter() - t0
+        st, ids = net.spikes()
+        net.close()
+        runs[dt] = (V, (st.astype(np.int64) + 1) * dt, ids, wall)   # spike times in ms
+    Vr, tr_, ir, _ = runs[DT_STUDY_MS[-1]]
+    table = []
+    for dt in DT_STUDY_MS:
+        V, ts, ids, wall = runs[dt]
+        rel = np.abs(V - Vr) / np.abs(Vr)          # [ms][neuron]
+        per_ms = rel.mean(axis=1)
+        hit = matched_spikes(tr_, ir, ts, ids, 1.0)
+        table.append({"dt_ms": dt, "rel_err_mean_1s": float(per_ms.mean()),
+                      "rel_err_mean_first_100ms": float(per_ms[:100].mean()),
+                      "rel_err_mean_first_800ms": float(per_ms[:800].mean()),
+                      "rel_err_at_1s": float(per_ms[-1]),
+                      "rate_hz": len(ids) / Vr.shape[1] / (DT_STUDY_STEPS / 1000.0),
+                      "reference_spikes_matched_within_1ms": hit / max(len(ir), 1),
+                      "wall_s": wall})
+    coarse = table[0]
+    line = {
+        "metric": "relative membrane-potential error, dt 1 ms vs %g ms" % DT_STUDY_MS[-1],
+        "value": coarse["rel_err_mean_1s"], "unit": "mean |dV| / |V| over neurons and 1 ms "
+                                                     "samples of one second",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": "step-size study (Extended Data Fig. 1): 1,000 neurons, in-degree "
+                               "100, delays 1 ms, constant injected current, no random drive; "
+                               "dt %s ms" % ", ".join("%g" % x for x in DT_STUDY_MS),
+                   "reference_dt_ms": DT_STUDY_MS[-1]},
+        "table": table,
+        "paper_context": "Extended Data Fig. 1 / Results: about 5 % relative membrane-potential "
+                         "error at dt 1 ms against 0.001 ms over one second",
+        "gpu_launches": int(sum(2 * DT_STUDY_STEPS * round(1.0 / x) for x in DT_STUDY_MS)),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------- micro-column workload ----
 def run_columns(args):
     """Cortical micro-column network (Extended Data Table 3): 100 voxels of
@@ -886,6 +1009,8 @@ def main():
         run_nest(args)
     elif args.workload == "columns":
         run_columns(args)
+    elif args.workload == "dt-study":
+        run_dt_study(args)
     else:
         run_ours(args)
 

@@ -64,6 +64,16 @@ typedef struct dbens dbens_t;
  *                    (round to nearest even) on the device
  *   delay            [E] uint8 delay in steps, 1..255; within each row the
  *                    delays must be non-decreasing
+ *   weight2          NULL: one weight per edge, shared by both channels of
+ *                    the source's class (AMPA and NMDA for an excitatory
+ *                    source, GABA_A and GABA_B for an inhibitory one).
+ *                    Otherwise [E] a second weight per edge, same dtype and
+ *                    rules as weight (the connection table of
+ *                    Supplementary Table 5 holds one weight per channel):
+ *                    weight then feeds AMPA / GABA_A and weight2 NMDA /
+ *                    GABA_B, and the engine keeps four accumulator channels
+ *                    per neuron instead of two.  Zero-initialised callers get
+ *                    NULL.
  * A spike of source j at step n reaches target col[e] through edge e in the
  * accumulator consumed at step n + delay[e].  Violations give DBNET_EINVAL. */
 typedef struct {
@@ -76,6 +86,7 @@ typedef struct {
   const void* weight;
   int32_t weight_dtype;
   const uint8_t* delay;
+  const void* weight2;
 } dbnet_graph_t;
 
 /* Per-region neuron and synapse constants (the property table of
@@ -157,10 +168,14 @@ typedef struct {
   int64_t bold_samples;      /* BOLD samples recorded */
   int32_t fixed_shift;       /* S in use */
   int32_t max_delay;         /* longest delay of the graph, steps */
-  int32_t packed_edges;      /* 1: edges held as 6-byte (target, BF16 weight) records */
+  int32_t packed_edges;      /* 1: edges held as 6-byte (target, BF16 weight)
+                                records, 8-byte (target, two BF16 weights) with
+                                two weights per edge */
   int32_t weights_rounded;   /* 1 when some float32 weight was not a BF16 value */
   int32_t deliver_blocks;    /* delivery grid in use */
   int32_t autotuned;         /* 1 once the autotuner has chosen that grid */
+  int32_t two_weights;       /* 1: four accumulator channels (two weights per edge) */
+  int32_t reserved;
 } dbnet_stats_t;
 
 /* Name of a status code (static string). */
@@ -375,7 +390,10 @@ typedef struct {
   int32_t chunk_steps;    /* Euler steps per scheduling round */
   int64_t arena_bytes;    /* device memory for the requests' graphs and buffers */
   int32_t max_inflight;   /* rounds enqueued ahead of the host */
-  int32_t reserved;
+  int32_t two_weights;    /* 1: four accumulator channels per neuron, so that
+                             requests may carry two weights per edge (8 more
+                             bytes per neuron and step in the update); 0:
+                             such a request fails with DBNET_EUNSUPPORTED */
   dbnet_options_t run;    /* dt, bin, TR, z_scale, hemodynamic constants,
                              fixed_shift, autotune_at, precision; seed, net_id
                              and capacities come with each request */

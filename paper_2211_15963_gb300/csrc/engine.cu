@@ -72,7 +72,8 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
 
   gd->row_ptr.alloc(N + 1);
   gd->ro.alloc(R + 1);
-  gd->rec.alloc(std::max<int64_t>(3 * E, 1));
+  gd->two_w = g->weight2 != nullptr;
+  gd->rec.alloc(std::max<int64_t>((gd->two_w ? 4 : 3) * E, 4));
   gd->seg.alloc(seg_bytes);
   CK(cudaMemcpyAsync(gd->row_ptr.p, g->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(gd->ro.p, g->region_offsets, sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s));
@@ -90,9 +91,10 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
     const int64_t cap = std::min(E, std::max(kIngestEdges, max_out));
     const int64_t wsz = g->weight_dtype == DBNET_WEIGHT_BF16 ? 2 : 4;
     DevBuf<int32_t> col_st;
-    DevBuf<uint8_t> w_st, d_st;
+    DevBuf<uint8_t> w_st, w2_st, d_st;
     col_st.alloc(cap);
     w_st.alloc(cap * wsz);
+    if (gd->two_w) w2_st.alloc(cap * wsz);
     d_st.alloc(cap);
     int32_t j0 = 0;
     while (j0 < N) {
@@ -104,7 +106,11 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
         CK(cudaMemcpyAsync(d_st.p, g->delay + e0, ne, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(w_st.p, static_cast<const uint8_t*>(g->weight) + e0 * wsz, ne * wsz,
                            cudaMemcpyHostToDevice, s));
-        launch_ingest(N, j0, j1, e0, gd->row_ptr.p, col_st.p, w_st.p, g->weight_dtype, d_st.p,
+        if (gd->two_w)
+          CK(cudaMemcpyAsync(w2_st.p, static_cast<const uint8_t*>(g->weight2) + e0 * wsz, ne * wsz,
+                             cudaMemcpyHostToDevice, s));
+        launch_ingest(N, j0, j1, e0, gd->row_ptr.p, col_st.p, w_st.p,
+                      gd->two_w ? w2_st.p : nullptr, g->weight_dtype, d_st.p,
                       gd->rec.p, gd->max_delay, gd->seg_stride, gd->seg.p, gd->seg_kind, indeg.p,
                       scal.p + 0, scal.p + 2, s);
         CK(cudaGetLastError());
@@ -288,10 +294,12 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     regions += sp.graph->R;
     dmax_all = std::max(dmax_all, sp.graph->max_delay);
   }
-  bool any_ext = false;
-  for (const auto& sp : specs)
+  bool any_ext = false, four = false;
+  for (const auto& sp : specs) {
     for (const auto& p : sp.params) any_ext = any_ext || ext_bits(p) != 0;
-  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream, any_ext);
+    four = four || sp.graph->two_w;
+  }
+  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream, any_ext, four);
   int64_t t = 0;
   int32_t r = 0;
   for (int k = 0; k < n; ++k) {
@@ -304,7 +312,8 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
 }
 
 void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
-                       const dbnet_options_t& common, void* user_stream, bool any_ext) {
+                       const dbnet_options_t& common, void* user_stream, bool any_ext,
+                       bool four) {
   if (user_stream) {
     stream = (cudaStream_t)user_stream;
     own_stream = false;
@@ -327,13 +336,13 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   Ibg.alloc(stride);
   fext.alloc(stride);
   ref.alloc(stride);
-  acc.alloc(stride);
+  acc.alloc((four ? 2 : 1) * stride);  // int2 per neuron, or int4 with four channels
   CK(cudaMemsetAsync(Ibg.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(fext.p, 0, sizeof(float) * stride, stream));  // read only where kExtHet
   CK(cudaMemsetAsync(V.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
   CK(cudaMemsetAsync(ref.p, 0, stride, stream));
-  CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * stride, stream));
+  CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * (four ? 2 : 1) * stride, stream));
   desc.alloc(n_inst);
   dyn.alloc(n_inst);
   tile_info.alloc(tiles);
@@ -390,6 +399,7 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev.Ibg = Ibg.p;
   dev.fext = fext.p;
   dev.any_ext = any_ext ? 1 : 0;
+  dev.four = four ? 1 : 0;
   dev.ref = ref.p;
   dev.acc = acc.p;
   dev.stride = stride;
@@ -439,6 +449,8 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
       rbase + g.R > cap_R)
     raise(DBNET_EINVAL, "instance placement outside the engine's capacity");
   if (g.max_delay >= dev.D) raise(DBNET_EINVAL, "a delay is longer than the engine's ring");
+  if (g.two_w && !dev.four)
+    raise(DBNET_EUNSUPPORTED, "two weights per edge need an engine with four accumulator channels");
   InstHost& ih = inst[(size_t)k];
   ih = InstHost{};
   ih.graph = sp.graph;
@@ -462,6 +474,7 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
   std::memset(&d, 0, sizeof(d));
   d.row_ptr = g.row_ptr.p;
   d.rec = g.rec.p;
+  d.two_w = g.two_w ? 1 : 0;
   d.col = nullptr;
   d.w = nullptr;
   d.delay = nullptr;
@@ -1015,6 +1028,7 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     out->weights_rounded = ih.graph->rounded ? 1 : 0;
     out->deliver_blocks = e.del_grid;
     out->autotuned = (!e.tune_pending && !e.tune_grid.empty()) ? 1 : 0;
+    out->two_weights = e.dev.four;
   });
 }
 

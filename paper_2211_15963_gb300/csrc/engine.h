@@ -9,10 +9,14 @@
 //
 // HBM layout (per global neuron i, stride = padded neuron count):
 //   V[i] f32 | J[u * stride + i] f32, u = AMPA, NMDA, GABA_A, GABA_B |
-//   ref[i] u8 (remaining refractory steps) | acc[i] int2 (E, I fixed point)
+//   ref[i] u8 (remaining refractory steps) | acc[i] int2 (E, I fixed point),
+//   or, in an engine with four channels, acc[2i], acc[2i+1] (AMPA, NMDA |
+//   GABA_A, GABA_B: one int4 per neuron)
 // Edges of an instance (CSR by source, rows sorted by delay), either
 //   rec[3e], rec[3e+1], rec[3e+2] u16 = target low, target high, BF16 weight
 //     (interleaved 6-byte records: a short segment is one contiguous read), or,
+//   with two weights per edge, rec[4e .. 4e+3] u16 = target low, target high,
+//     BF16 weight, BF16 second weight (8-byte records, one load each), or,
 //   for graphs the caller keeps (the allocation-free entry point), arrays
 //   col[e] u32 = target, w[e] u16 BF16 bit pattern, delay[e] u8
 //   seg[j * seg_stride + k] u16/u32 = number of edges of row j with
@@ -124,6 +128,7 @@ struct alignas(16) InstDesc {
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;
   int32_t seg_kind, dmax, seg_stride, ext;  // ext: kExt* bits of any region
+  int32_t two_w, pad_w;          // two_w: 8-byte records with a second weight
   double h_bw, z_scale, kappa, gamma, tau, alpha, rho, V0;
 };
 
@@ -178,6 +183,7 @@ struct EngineDev {
   int32_t D;
   int32_t n_inst, n_tiles, total_R;
   int32_t any_ext;       // launch the update variant with the kExt* terms
+  int32_t four;          // four accumulator channels per neuron (acc as int4)
 };
 
 // Launchers (kernels.cu)
@@ -190,7 +196,7 @@ void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s);
 void launch_set_base(unsigned long long* base, unsigned long long g, cudaStream_t s);
 int deliver_grid();
 void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,
-                   const int32_t* col_in, const void* w_in, int32_t w_dtype,
+                   const int32_t* col_in, const void* w_in, const void* w2_in, int32_t w_dtype,
                    const uint8_t* delay_in, uint16_t* rec, int32_t dmax, int32_t seg_stride,
                    void* seg, int32_t seg_kind, int32_t* indeg, unsigned* wmax_bits, unsigned* err,
                    cudaStream_t s);

@@ -167,12 +167,14 @@ struct GraphDev {
   int64_t E = 0;
   std::vector<int32_t> ro_h, nexc_h;
   DevBuf<int64_t> row_ptr;
-  DevBuf<uint16_t> rec;  // [3E] interleaved (target lo, target hi, BF16 weight)
+  DevBuf<uint16_t> rec;  // [3E] interleaved (target lo, target hi, BF16 weight),
+                         // or [4E] with a second BF16 weight per edge
   DevBuf<int32_t> ro;
   DevBuf<uint8_t> seg;  // [N][seg_stride] u16 or u32 segment table
   int32_t seg_kind = 0, seg_stride = 0;
   bool packed = true;  // edges held as interleaved records
   bool rounded = false;
+  bool two_w = false;  // a second weight per edge (8-byte records)
   int32_t max_delay = 1, kin_max = 0;
   double w_max = 0.0;
 };
@@ -250,9 +252,11 @@ struct Engine {
   // Empty capacity for instances placed later: every tile and region slot
   // starts unused (the kernels skip it); D = longest delay + 1.
   // any_ext: launch the update variant with the OU current and the
-  // per-neuron injected-current factors.
+  // per-neuron injected-current factors; four: four accumulator channels
+  // per neuron, so that instances may carry two weights per edge.
   void init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
-                 const dbnet_options_t& common, void* user_stream, bool any_ext);
+                 const dbnet_options_t& common, void* user_stream, bool any_ext,
+                 bool four = false);
   // Put instance k on tiles [first_tile, +tiles of its graph) and region
   // slots [rbase, +R): its constants, buffers and initial state; its step 0
   // is the next iteration enqueued, and it stops after n_end steps.

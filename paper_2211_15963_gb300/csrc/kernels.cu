@@ -6,7 +6,9 @@
 //              Philox4x64-10, spike compaction into the spike ring,
 //              and region spike counts; k_update<true> also integrates the
 //              background OU current (Eq. 1) and applies the per-neuron
-//              injected-current factors.
+//              injected-current factors; k_update<., true> reads four
+//              accumulator channels (two weights per edge) instead of the
+//              two classes.
 //   k_close / the head of k_deliver: the per-bin Balloon-Windkessel step
 //              (Extended Data Table 4) and the BOLD sample, one region per
 //              thread.
@@ -17,7 +19,9 @@
 //              leading blocks fill for the previous step's spikes (or from
 //              the graph's segment table) -- are added to this step's
 //              fixed-point accumulators, the warp's segments laid end to end
-//              so that consecutive lanes read consecutive edge records.
+//              so that consecutive lanes read consecutive edge records;
+//              k_deliver<true> adds an edge's two weights to the channel pair
+//              of the source's class with one 64-bit atomic.
 //
 // Both kernels find their iteration through a StepRef (a base word in device
 // memory plus an offset), so a captured CUDA graph of (deliver, update) pairs
@@ -94,8 +98,11 @@ __global__ void __launch_bounds__(kUpdThreads) k_init_state(EngineDev e, int ins
   for (int u = 0; u < 4; ++u)
     *reinterpret_cast<float4*>(e.J + u * e.stride + gi0) = make_float4(0.f, 0.f, 0.f, 0.f);
   *reinterpret_cast<uint32_t*>(e.ref + gi0) = 0u;
-  *reinterpret_cast<int4*>(e.acc + gi0) = make_int4(0, 0, 0, 0);
-  *reinterpret_cast<int4*>(e.acc + gi0 + 2) = make_int4(0, 0, 0, 0);
+  // accumulators: int2 per neuron, or int4 (acc[2i], acc[2i + 1]) with four
+  // channels
+  const int words = e.four ? 4 : 2;
+  for (int k = 0; k < words; ++k)
+    *reinterpret_cast<int4*>(e.acc + (e.four ? 2 : 1) * gi0 + 2 * k) = make_int4(0, 0, 0, 0);
 }
 
 __device__ __forceinline__ unsigned long long step_of(const StepRef& sr) {
@@ -144,8 +151,10 @@ __device__ __forceinline__ float normal_from_word(unsigned long long w) {
 }
 
 // EXT: also the kExt* terms of the instances that have them: the background
-// OU current and the per-neuron injected-current factor.
-template <bool EXT>
+// OU current and the per-neuron injected-current factor.  FOUR: the
+// accumulators hold four channels per neuron (two weights per edge); the
+// background drive adds to both AMPA and NMDA.
+template <bool EXT, bool FOUR>
 __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef sr) {
   __shared__ RegionConst s_rc[kTileRegions];
   __shared__ uint32_t s_wtot[kUpdThreads / 32];
@@ -168,8 +177,20 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     B4 = __ldcs(reinterpret_cast<const float4*>(e.Ibg + gi0));
     F4 = __ldg(reinterpret_cast<const float4*>(e.fext + gi0));
   }
-  const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
-  const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
+  // this step's arrivals, per channel (AMPA, NMDA, GABA_A, GABA_B) of the
+  // thread's four neurons
+  int4 A[4];
+  if (FOUR) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) A[k] = *reinterpret_cast<const int4*>(e.acc + 2 * gi0 + 2 * k);
+  } else {
+    const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
+    const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
+    A[0] = make_int4(a01.x, a01.x, a01.y, a01.y);
+    A[1] = make_int4(a01.z, a01.z, a01.w, a01.w);
+    A[2] = make_int4(a23.x, a23.x, a23.y, a23.y);
+    A[3] = make_int4(a23.z, a23.z, a23.w, a23.w);
+  }
 
   const int4 ti = e.tile_info[tile];  // instance, first region, regions touched
   const unsigned long long g = step_of(sr);
@@ -194,8 +215,9 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   int reg[4] = {0, 0, 0, 0};
 
   if (active && li0 < d.N) {
-    *reinterpret_cast<int4*>(e.acc + gi0) = make_int4(0, 0, 0, 0);
-    *reinterpret_cast<int4*>(e.acc + gi0 + 2) = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < (FOUR ? 4 : 2); ++k)
+      *reinterpret_cast<int4*>(e.acc + (FOUR ? 2 : 1) * gi0 + 2 * k) = make_int4(0, 0, 0, 0);
     unsigned long long x[4] = {(unsigned long long)n, (unsigned long long)(li0 >> 2), 0ull, 0ull};
     philox4x64_10(x, d.seed, d.net_id);
     float ib[4] = {B4.x, B4.y, B4.z, B4.w};
@@ -214,8 +236,6 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
                      {J4[2].x, J4[2].y, J4[2].z, J4[2].w},
                      {J4[3].x, J4[3].y, J4[3].z, J4[3].w}};
     int rr[4] = {rf.x, rf.y, rf.z, rf.w};
-    const int aE[4] = {a01.x, a01.z, a23.x, a23.z};
-    const int aI[4] = {a01.y, a01.w, a23.y, a23.w};
     int r = 0;  // relative to r0
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -235,7 +255,8 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
       const uint32_t uu = (uint32_t)(x[k] >> 32);
       int c = 0;
       while (c < W.x && uu >= p.thr[c]) ++c;
-      const int ae = aE[k] + c * __float_as_int(Q.w);
+      const int dq = c * __float_as_int(Q.w);
+      const int a0 = A[k].x + dq, a1 = A[k].y + dq;  // the drive feeds AMPA and NMDA
       // membrane with the old V and traces
       const float vk = v[k];
       const float gu[4] = {G.x, G.y, G.z, G.w}, vu[4] = {VU.x, VU.y, VU.z, VU.w};
@@ -263,12 +284,14 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
         ib[k] = __fadd_rn(ib[k], __fmul_rn(OUc.z, xi));
       }
       // traces: decay, then this step's arrivals
-      const float xE = __fmul_rn(__int2float_rn(ae), d.inv_two_S);
-      const float xI = __fmul_rn(__int2float_rn(aI[k]), d.inv_two_S);
-      j[0][k] = __fadd_rn(__fmul_rn(DE.x, j[0][k]), xE);
-      j[1][k] = __fadd_rn(__fmul_rn(DE.y, j[1][k]), xE);
-      j[2][k] = __fadd_rn(__fmul_rn(DE.z, j[2][k]), xI);
-      j[3][k] = __fadd_rn(__fmul_rn(DE.w, j[3][k]), xI);
+      const float x0 = __fmul_rn(__int2float_rn(a0), d.inv_two_S);
+      const float x1 = FOUR ? __fmul_rn(__int2float_rn(a1), d.inv_two_S) : x0;
+      const float x2 = __fmul_rn(__int2float_rn(A[k].z), d.inv_two_S);
+      const float x3 = FOUR ? __fmul_rn(__int2float_rn(A[k].w), d.inv_two_S) : x2;
+      j[0][k] = __fadd_rn(__fmul_rn(DE.x, j[0][k]), x0);
+      j[1][k] = __fadd_rn(__fmul_rn(DE.y, j[1][k]), x1);
+      j[2][k] = __fadd_rn(__fmul_rn(DE.z, j[2][k]), x2);
+      j[3][k] = __fadd_rn(__fmul_rn(DE.w, j[3][k]), x3);
       // refractory clamp, threshold, reset
       if (rr[k] > 0) {
         v[k] = Q.x;
@@ -357,6 +380,12 @@ __device__ int64_t first_delay_at_least(const uint32_t* col, const uint8_t* dl, 
   return lo;
 }
 
+// FOUR: the engine keeps four accumulator channels per neuron; an edge adds
+// its two weights (the one weight twice for one-weight records) to the
+// channel pair of the source's class with one 64-bit atomic.  Every channel
+// sum stays below 2^31 (the fixed-point scale is chosen so), so the low word
+// never carries into the high one.
+template <bool FOUR>
 __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr) {
   __shared__ unsigned long long s_pre[256];  // items whose delay is below index + 1
   __shared__ unsigned long long s_wsum[kDelThreads / 32];
@@ -530,18 +559,32 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
       if (fi < total) {
         const InstDesc& dd = e.insts[qi];
         const int64_t ei = q0 + (int64_t)(fi - qx);
-        uint32_t tg, wb;
-        if (dd.rec) {
+        uint32_t tg, wb, wb2 = 0;
+        if (FOUR && dd.two_w) {  // 8-byte record: target, weight | second weight << 16
+          const uint2 r4 = __ldg(reinterpret_cast<const uint2*>(dd.rec) + ei);
+          tg = r4.x;
+          wb = r4.y & 0xFFFFu;
+          wb2 = r4.y >> 16;
+        } else if (dd.rec) {
           const uint16_t* r3 = dd.rec + 3 * ei;
           tg = (uint32_t)__ldg(r3) | ((uint32_t)__ldg(r3 + 1) << 16);
           wb = __ldg(r3 + 2);
+          wb2 = wb;
         } else {
           tg = __ldg(dd.col + ei) & dd.tmask;
           wb = __ldg(dd.w + ei);
+          wb2 = wb;
         }
-        const float wf = __uint_as_float(wb << 16);
-        int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
-        atomicAdd(accp + 2 * (size_t)tg, __float2int_rn(__fmul_rn(wf, dd.two_S)));
+        const int q = __float2int_rn(__fmul_rn(__uint_as_float(wb << 16), dd.two_S));
+        if (FOUR) {
+          const int q2 = __float2int_rn(__fmul_rn(__uint_as_float(wb2 << 16), dd.two_S));
+          unsigned long long* accp = reinterpret_cast<unsigned long long*>(e.acc) +
+                                     2 * (size_t)(dd.base + (int64_t)tg) + qc;
+          atomicAdd(accp, ((unsigned long long)(uint32_t)q2 << 32) | (uint32_t)q);
+        } else {
+          int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
+          atomicAdd(accp + 2 * (size_t)tg, q);
+        }
       }
     }
     if (lane == 0) ev += total;
@@ -558,18 +601,41 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
   }
 }
 
+// BF16 bit pattern of staged weight e (float32 rounded to nearest even, or
+// taken as given), with the rounding and range checks of ingest.
+__device__ __forceinline__ uint16_t staged_bf16(const void* w_in, int32_t w_dtype, int64_t e,
+                                                unsigned& err, unsigned& wmax) {
+  uint16_t wb;
+  if (w_dtype == 1) {
+    wb = static_cast<const uint16_t*>(w_in)[e];
+  } else {
+    const float f = static_cast<const float*>(w_in)[e];
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+    wb = (uint16_t)(r >> 16);
+    if ((uint32_t)wb << 16 != u) err |= kErrRounded;
+  }
+  const uint32_t wu = (uint32_t)wb << 16;
+  const float wf = __uint_as_float(wu);
+  if (!(wf >= 0.0f) || isinf(wf)) err |= kErrWeight;
+  else wmax = max(wmax, wu);
+  return wb;
+}
+
 // Ingest rows [j0, j1) of a graph from staging arrays that hold its edges
 // from e_base on: warp per source row.  Checks every edge (target range,
-// delay >= 1 and non-decreasing within the row, weight finite and
+// delay >= 1 and non-decreasing within the row, weights finite and
 // non-negative after rounding to BF16), counts in-degrees, and writes
 //   rec[3e .. 3e+2] = target low 16 bits, target high 16 bits, BF16 weight
+//   (with second weights w2_in: rec[4e .. 4e+3], the second weight last)
 //   seg[j * seg_stride + k] = number of edges of row j with delay <= k + 1
 // (the segment table must be zero on entry; entries below the row's first
 // delay stay zero).
 __global__ void k_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base,
                          const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_in,
-                         const void* __restrict__ w_in, int32_t w_dtype,
-                         const uint8_t* __restrict__ delay_in, uint16_t* __restrict__ rec,
+                         const void* __restrict__ w_in, const void* __restrict__ w2_in,
+                         int32_t w_dtype, const uint8_t* __restrict__ delay_in,
+                         uint16_t* __restrict__ rec,
                          int32_t dmax, int32_t seg_stride, void* seg, int32_t kind,
                          int32_t* indeg, unsigned* wmax_bits, unsigned* err) {
   const int lane = threadIdx.x & 31;
@@ -584,25 +650,17 @@ __global__ void k_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base,
       if (t < 0 || t >= N) my_err |= kErrTarget;
       if (d < 1u) my_err |= kErrDelayRange;
       if (e > a && delay_in[e - 1] > d) my_err |= kErrDelayOrder;
-      uint16_t wb;
-      if (w_dtype == 1) {
-        wb = static_cast<const uint16_t*>(w_in)[e];
-      } else {
-        const float f = static_cast<const float*>(w_in)[e];
-        const uint32_t u = __float_as_uint(f);
-        const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
-        wb = (uint16_t)(r >> 16);
-        if ((uint32_t)wb << 16 != u) my_err |= kErrRounded;
-      }
-      const uint32_t wu = (uint32_t)wb << 16;
-      const float wf = __uint_as_float(wu);
-      if (!(wf >= 0.0f) || isinf(wf)) my_err |= kErrWeight;
-      else my_wmax = max(my_wmax, wu);
+      const uint16_t wb = staged_bf16(w_in, w_dtype, e, my_err, my_wmax);
       const uint32_t tu = (uint32_t)t;
-      uint16_t* r3 = rec + 3 * (e_base + e);
-      r3[0] = (uint16_t)(tu & 0xFFFFu);
-      r3[1] = (uint16_t)(tu >> 16);
-      r3[2] = wb;
+      if (w2_in) {
+        const uint16_t wb2 = staged_bf16(w2_in, w_dtype, e, my_err, my_wmax);
+        reinterpret_cast<uint2*>(rec)[e_base + e] = make_uint2(tu, (uint32_t)wb | ((uint32_t)wb2 << 16));
+      } else {
+        uint16_t* r3 = rec + 3 * (e_base + e);
+        r3[0] = (uint16_t)(tu & 0xFFFFu);
+        r3[1] = (uint16_t)(tu >> 16);
+        r3[2] = wb;
+      }
       if (t >= 0 && t < N) atomicAdd(indeg + t, 1);
     }
     // segment counts: edge p closes the delays from its own to the next edge's
@@ -651,8 +709,13 @@ void launch_init_state(const EngineDev& e, int inst, int n_tiles_inst, int first
 }
 
 void launch_update(const EngineDev& e, StepRef sr, cudaStream_t s) {
-  if (e.any_ext) k_update<true><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
-  else k_update<false><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+  if (e.four) {
+    if (e.any_ext) k_update<true, true><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+    else k_update<false, true><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+  } else {
+    if (e.any_ext) k_update<true, false><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+    else k_update<false, false><<<e.n_tiles, kUpdThreads, 0, s>>>(e, sr);
+  }
 }
 
 void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s) {
@@ -669,7 +732,7 @@ int deliver_grid() {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deliver, kDelThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deliver<false>, kDelThreads, 0);
     if (occ < 1) occ = 1;
     g_deliver_grid = sms * occ;
   }
@@ -678,19 +741,21 @@ int deliver_grid() {
 
 void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s) {
   if (grid < 2) grid = 2;  // with a segment ring, block 0 may take no items
-  k_deliver<<<grid, kDelThreads, 0, s>>>(e, sr);
+  if (e.four) k_deliver<true><<<grid, kDelThreads, 0, s>>>(e, sr);
+  else k_deliver<false><<<grid, kDelThreads, 0, s>>>(e, sr);
 }
 
 void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,
-                   const int32_t* col_in, const void* w_in, int32_t w_dtype,
+                   const int32_t* col_in, const void* w_in, const void* w2_in, int32_t w_dtype,
                    const uint8_t* delay_in, uint16_t* rec, int32_t dmax, int32_t seg_stride,
                    void* seg, int32_t seg_kind, int32_t* indeg, unsigned* wmax_bits, unsigned* err,
                    cudaStream_t s) {
   int64_t blocks = ((int64_t)(j1 - j0) * 32 + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  k_ingest<<<(int)blocks, 256, 0, s>>>(N, j0, j1, e_base, row_ptr, col_in, w_in, w_dtype, delay_in,
-                                       rec, dmax, seg_stride, seg, seg_kind, indeg, wmax_bits, err);
+  k_ingest<<<(int)blocks, 256, 0, s>>>(N, j0, j1, e_base, row_ptr, col_in, w_in, w2_in, w_dtype,
+                                       delay_in, rec, dmax, seg_stride, seg, seg_kind, indeg,
+                                       wmax_bits, err);
 }
 
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s) {

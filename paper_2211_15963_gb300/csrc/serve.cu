@@ -185,8 +185,9 @@ int64_t arena_estimate(const Req& r, int32_t dmax) {
   const dbnet_graph_t& g = r.graph;
   const int64_t N = g.n_neurons, E = g.row_ptr[N], R = g.n_regions;
   const int64_t stride = (dmax + 7) / 8 * 8;
-  const int64_t stage = std::min<int64_t>(E, int64_t(1) << 27) * 9;
-  return 6 * E + 8 * (N + 1) + 4 * stride * N + stage + 8 * N + 4 * (R + 1) +
+  const bool two = g.weight2 != nullptr;
+  const int64_t stage = std::min<int64_t>(E, int64_t(1) << 27) * (two ? 13 : 9);
+  return (two ? 8 : 6) * E + 8 * (N + 1) + 4 * stride * N + stage + 8 * N + 4 * (R + 1) +
          (int64_t)sizeof(RegionConst) * R + 8 * std::max<int64_t>(r.rq.bold_capacity, 1) * R +
          8 * r.rq.raster_capacity + (int64_t(1) << 20);
 }
@@ -444,12 +445,14 @@ int dbsrv_create(const dbsrv_options_t* options, void* cuda_stream, dbsrv_t** ou
         o.max_inflight < 1 || o.arena_bytes < (int64_t(1) << 20))
       raise(DBNET_EINVAL, "server capacities must be positive (arena >= 1 MiB)");
     if (o.max_delay < 1 || o.max_delay > 255) raise(DBNET_EINVAL, "max_delay must be 1..255");
+    if (o.two_weights != 0 && o.two_weights != 1) raise(DBNET_EINVAL, "two_weights must be 0 or 1");
     const int64_t tiles = (o.max_neurons + kTile - 1) / kTile;
     if (tiles * kTile >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "max_neurons too large");
     s->opt = o;
     s->eng.reset(new Engine());
     s->eng->init_pool(o.max_requests, tiles, o.max_regions, o.max_delay + 1, o.run, cuda_stream,
-                      true);  // any request may bring the OU current
+                      true,  // any request may bring the OU current
+                      o.two_weights != 0);
     s->eng->set_extent(1, 1);
     s->arena.init(o.arena_bytes);
     CK(cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking));
@@ -475,6 +478,8 @@ int dbsrv_submit(dbsrv_t* s, const dbnet_graph_t* graph, const dbnet_region_para
       raise(DBNET_EINVAL, "negative capacity");
     if ((int64_t)tiles_for(N) > s->eng->cap_tiles || R > s->eng->cap_R)
       raise(DBNET_ERANGE, "the request is larger than the server's pool");
+    if (g.weight2 && !s->opt.two_weights)
+      raise(DBNET_EUNSUPPORTED, "two weights per edge need a server created with two_weights = 1");
     for (int32_t r = 0; r < R; ++r) check_params(params[r], s->opt.run.dt_ms);
     auto q = std::make_unique<Req>();
     q->id = s->next_id++;

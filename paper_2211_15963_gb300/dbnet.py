@@ -40,7 +40,7 @@ _d, _i32, _i64, _u64, _vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, cty
 class dbnet_graph_t(ctypes.Structure):
     _fields_ = [("n_neurons", _i32), ("n_regions", _i32), ("region_offsets", _vp),
                 ("n_exc", _vp), ("row_ptr", _vp), ("col", _vp), ("weight", _vp),
-                ("weight_dtype", _i32), ("delay", _vp)]
+                ("weight_dtype", _i32), ("delay", _vp), ("weight2", _vp)]
 
 
 class dbnet_region_params_t(ctypes.Structure):
@@ -62,7 +62,8 @@ class dbnet_stats_t(ctypes.Structure):
     _fields_ = [("step", _i64), ("spikes", _i64), ("events", _i64), ("raster_len", _i64),
                 ("raster_dropped", _i64), ("bold_samples", _i64), ("fixed_shift", _i32),
                 ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32),
-                ("deliver_blocks", _i32), ("autotuned", _i32)]
+                ("deliver_blocks", _i32), ("autotuned", _i32), ("two_weights", _i32),
+                ("reserved", _i32)]
 
 
 class dbnet_device_graph_t(ctypes.Structure):
@@ -74,7 +75,7 @@ class dbnet_device_graph_t(ctypes.Structure):
 class dbsrv_options_t(ctypes.Structure):
     _fields_ = [("max_neurons", _i64), ("max_requests", _i32), ("max_regions", _i32),
                 ("max_delay", _i32), ("chunk_steps", _i32), ("arena_bytes", _i64),
-                ("max_inflight", _i32), ("reserved", _i32), ("run", dbnet_options_t)]
+                ("max_inflight", _i32), ("two_weights", _i32), ("run", dbnet_options_t)]
 
 
 class dbsrv_request_t(ctypes.Structure):
@@ -258,19 +259,23 @@ def params_array(params, n_regions: int):
 def graph_struct(graph):
     """dbnet_graph_t over the arrays of a graph object with fields n_neurons,
     n_regions, region_offsets, n_exc, row_ptr, col, w_bf16 (or weight) and
-    delay.  Returns (struct, keepalive)."""
+    delay, and optionally w2_bf16 (or weight2): a second weight per edge.
+    Returns (struct, keepalive)."""
     ro = np.ascontiguousarray(graph.region_offsets, dtype=np.int32)
     ne = np.ascontiguousarray(graph.n_exc, dtype=np.int32)
     rp = graph.row_ptr
     if isinstance(rp, np.ndarray):
         rp = np.ascontiguousarray(rp, dtype=np.int64)
     w = getattr(graph, "w_bf16", None)
+    w2 = getattr(graph, "w2_bf16", None)
     dtype = DBNET_WEIGHT_BF16
     if w is None:
         w = graph.weight
+        w2 = getattr(graph, "weight2", None)
         dtype = DBNET_WEIGHT_F32
     g = dbnet_graph_t(int(graph.n_neurons), int(graph.n_regions), _addr(ro), _addr(ne), _addr(rp),
-                      _addr(graph.col), _addr(w), dtype, _addr(graph.delay))
+                      _addr(graph.col), _addr(w), dtype, _addr(graph.delay),
+                      _addr(w2) if w2 is not None else None)
     return g, (ro, ne, rp, graph)
 
 

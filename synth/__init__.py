@@ -305,13 +305,21 @@ def graph_from_dense(W: np.ndarray, Dl: np.ndarray, sizes, exc_frac: float = 0.8
     return Graph(N, len(sizes), ro, n_exc, row_ptr, col, w, d, dmax, w2)
 
 
-def with_second_weight(g: Graph, seed: int, w_mu: float = -1.0, w_sigma: float = 0.5) -> Graph:
+def with_second_weight(g: Graph, seed: int, w_mu: float = -1.0, w_sigma: float = 0.5,
+                       alloc=None) -> Graph:
     """The same graph with a second weight on every edge, drawn independently
     from the lognormal(w_mu, w_sigma) of the first and rounded to BF16 (the
     connection table of Supplementary Table 5 stores one weight per channel,
-    the channels' weights sharing a distribution)."""
+    the channels' weights sharing a distribution).  Drawn in chunks;
+    `alloc(n, dtype)` may supply the output array."""
     rng = np.random.default_rng(seed)
-    w2 = f64_to_bf16(rng.lognormal(w_mu, w_sigma, g.n_edges))
+    E = g.n_edges
+    w2 = np.empty(E, dtype=np.uint16) if alloc is None else alloc(E, np.uint16)
+    out = w2 if isinstance(w2, np.ndarray) else w2.numpy().view(np.uint16)
+    CH = 1 << 24
+    for e0 in range(0, E, CH):
+        e1 = min(E, e0 + CH)
+        out[e0:e1] = f64_to_bf16(rng.lognormal(w_mu, w_sigma, e1 - e0))
     return dataclasses.replace(g, w2_bf16=w2)
 
 

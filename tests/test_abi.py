@@ -119,7 +119,8 @@ def test_ensemble_host_validation(lib):
 def test_server_host_validation(lib):
     """dbsrv_create checks its options on the host before touching a device."""
     for bad in (dict(max_requests=0), dict(max_delay=0), dict(max_delay=256),
-                dict(chunk_steps=0), dict(arena_bytes=1024), dict(max_neurons=0)):
+                dict(chunk_steps=0), dict(arena_bytes=1024), dict(max_neurons=0),
+                dict(two_weights=2)):
         with pytest.raises(dbnet.DbnetError) as ei:
             dbnet.Server(**bad)
         assert ei.value.code == dbnet.DBNET_EINVAL, bad

@@ -6,6 +6,7 @@ import os
 import socket
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -65,3 +66,26 @@ def test_serving_drive_interpolation():
         assert abs(bench.serve_drive(k) - v) < 1e-12
     assert bench.SERVE_DRIVE[0][1] < bench.serve_drive(200) < bench.SERVE_DRIVE[1][1]
     assert bench.serve_drive(50) == bench.SERVE_DRIVE[0][1]
+
+
+def test_step_size_study_networks_share_topology():
+    """Every step of the study runs the same graph, weights and initial
+    state; only the delay in steps (1 ms each) and dt change."""
+    import bench
+    g1, p1, d1 = bench.dt_study_network(1.0, 5)
+    g2, p2, d2 = bench.dt_study_network(0.008, 5)
+    assert (d1, d2) == (1, 125) and p1 == p2 and p1["drive_rate_hz"] == 0.0
+    assert np.array_equal(g1.col, g2.col) and np.array_equal(g1.w_bf16, g2.w_bf16)
+    assert np.all(np.asarray(g2.delay) == 125) and g2.max_delay == 125
+    assert bench.DT_STUDY_MS[-1] * 250 >= p1["Tref"] - 1e-12   # refractory fits 8 bits
+
+
+def test_matched_spikes_counts_reference_spikes_within_tolerance():
+    import bench
+    ref_t = np.array([1.0, 5.0, 9.0, 2.0, 3.0])
+    ref_i = np.array([0, 0, 0, 1, 2])
+    t = np.array([1.5, 7.0, 9.9, 4.0])
+    i = np.array([0, 0, 0, 1])
+    assert bench.matched_spikes(ref_t, ref_i, t, i, 1.0) == 2
+    assert bench.matched_spikes(ref_t, ref_i, t, i, 2.0) == 4
+    assert bench.matched_spikes(ref_t, ref_i, ref_t, ref_i, 0.0) == 5

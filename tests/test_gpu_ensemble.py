@@ -69,6 +69,31 @@ def test_members_equal_single_networks():
     ens.close()
 
 
+def test_two_weight_members_equal_single_networks():
+    """Ensemble members over a graph with two weights per edge equal the
+    same networks run alone."""
+    from paper_2211_15963_gb300 import dbnet
+    g = synth.with_second_weight(_graph(), 5)
+    base = [synth.default_region_params(I_ext=0.85 + 0.03 * r) for r in range(g.n_regions)]
+    M = 2
+    theta = np.random.default_rng(2).uniform(LO, HI, (M, g.n_regions, 2))
+    opts = dict(seed=8, net_id=200, tr_ms=10.0, raster_capacity=1 << 20)
+    ens = dbnet.Ensemble(g, base, M, theta, opts)
+    ens.step(400)
+    for m in range(M):
+        net = dbnet.Network(g, _member_params(base, theta[m]), dict(opts, net_id=200 + m))
+        net.step(400)
+        assert net.stats()["two_weights"] == 1
+        for x, y in zip(ens.member_state(m), net.state()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(ens.member_bold(m), net.bold())
+        sa, sb = ens.member_spikes(m), net.spikes()
+        assert len(sb[1]) > 100
+        assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+        net.close()
+    ens.close()
+
+
 @pytest.mark.parametrize("mode", ["diffusion", "global"])
 def test_analysis_matches_oracle_enkf(mode):
     from paper_2211_15963_gb300 import dbnet

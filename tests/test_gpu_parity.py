@@ -405,3 +405,122 @@ def test_lowered_fixed_point_scale_bit_exact():
     with pytest.raises(dbnet.DbnetError) as ei:
         dbnet.Network(g, p, dict(fixed_shift=20))
     assert ei.value.code == dbnet.DBNET_EOVERFLOW
+
+
+# ------------------------------------------------ two weights per edge -----
+def test_two_weights_per_edge_bit_exact():
+    """Two weights per edge (Supplementary Table 5 keeps one per channel):
+    AMPA / GABA_A take the first, NMDA / GABA_B the second.  On the device:
+    four accumulator channels, 8-byte records, one 64-bit atomic per edge.
+    Uneven regions with a ragged tail, delays up to 120 steps."""
+    g = synth.with_second_weight(
+        synth.make_graph([1500, 700, 333, 2049], 80, 21, k_within=64, d_within=(1, 30),
+                         d_cross=(30, 120)), 77)
+    params = [synth.default_region_params(I_ext=0.8 + 0.05 * r) for r in range(g.n_regions)]
+    net = _net(g, params, seed=4, tr_ms=5.0)
+    o = oracle.Sim(g, params, seed=4, tr_ms=5.0, precision=32)
+    s = net.stats()
+    assert s["two_weights"] == 1 and s["packed_edges"] == 1
+    assert s["fixed_shift"] == o.info()["S"]
+    net.step(700)
+    o.step(700)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 500
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "two weights")
+    assert np.allclose(net.bold(), o.bold(), rtol=1e-10, atol=1e-15)
+    assert net.stats()["events"] == _delivered_by(g, st, ids, 700)
+    net.close()
+
+
+def test_two_weights_at_scale_bit_exact():
+    """100,000 neurons, in-degree 400, two weights per edge: many blocks
+    racing 64-bit atomics on the same channel pairs, the delay-major segment
+    ring and the autotuned grid, against the oracle over 250 steps."""
+    g = synth.with_second_weight(
+        synth.make_graph([20000] * 5, 400, 41, k_within=320, d_within=(1, 40),
+                         d_cross=(40, 120)), 78)
+    p = synth.scale_for_degree(synth.default_region_params(I_ext=7.2), 400)
+    net = _net(g, p, seed=6, autotune_at=64)
+    o = oracle.Sim(g, p, seed=6, precision=32)
+    net.step(250)
+    o.step(250)
+    assert net.stats()["autotuned"] == 1
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 5000
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "two weights at scale")
+    net.close()
+
+
+def test_two_equal_weights_equal_the_one_weight_run(small_graph):
+    """With the second weight equal to the first, the four-channel kernels
+    give exactly the one-weight run."""
+    import dataclasses
+    g2 = dataclasses.replace(small_graph, w2_bf16=np.array(small_graph.w_bf16).copy())
+    p = synth.default_region_params()
+    a = _net(small_graph, p, seed=8)
+    b = _net(g2, p, seed=8)
+    a.step(1000)
+    b.step(1000)
+    assert a.stats()["two_weights"] == 0 and b.stats()["two_weights"] == 1
+    sa, sb = a.spikes(), b.spikes()
+    assert len(sa[1]) > 200
+    assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
+
+
+def test_two_float_weights_round_and_validate(small_graph):
+    """float32 first and second weights: BF16-exact values give the BF16
+    graph's run; a second weight that is not a BF16 value sets the rounding
+    flag; a negative or non-finite second weight is refused."""
+    from paper_2211_15963_gb300 import dbnet
+    g = synth.with_second_weight(small_graph, 79)
+    p = synth.default_region_params()
+
+    class F:
+        n_neurons, n_regions = g.n_neurons, g.n_regions
+        region_offsets, n_exc, row_ptr, col, delay = g.region_offsets, g.n_exc, g.row_ptr, g.col, g.delay
+        weight = g.weights_f64().astype(np.float32)
+        weight2 = synth.bf16_to_f64(g.w2_bf16).astype(np.float32)
+
+    a = _net(g, p, seed=8)
+    b = _net(F, p, seed=8)
+    a.step(300)
+    b.step(300)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    assert b.stats()["weights_rounded"] == 0 and b.stats()["two_weights"] == 1
+    F.weight2 = F.weight2 * np.float32(1.001)
+    assert dbnet.Network(F, p, dict(seed=8)).stats()["weights_rounded"] == 1
+    for bad in (-1.0, np.inf):
+        F.weight2 = synth.bf16_to_f64(g.w2_bf16).astype(np.float32)
+        F.weight2[17] = bad
+        with pytest.raises(dbnet.DbnetError) as ei:
+            dbnet.Network(F, p, dict(seed=8))
+        assert ei.value.code == dbnet.DBNET_EINVAL
+
+
+@pytest.mark.parametrize("dt,steps", [(1.0, 1000), (0.01, 3000)])
+def test_step_size_study_networks_bit_exact(dt, steps):
+    """Both ends of the step-size study: dt = 1 ms (delay 1 step) and
+    dt = 0.01 ms (every delay 100 steps, refractory period 200 steps, a bin
+    of 100 steps), constant current and no random drive."""
+    import bench
+    g, p, d = bench.dt_study_network(dt, 4242)
+    net = _net(g, p, dt_ms=dt, bin_ms=1.0, seed=5)
+    o = oracle.Sim(g, p, dt_ms=dt, bin_ms=1.0, seed=5, precision=32)
+    net.step(steps)
+    o.step(steps)
+    st, ids = net.spikes()
+    rs, rids = o.raster()
+    assert len(ids) > 100
+    assert np.array_equal(st, rs) and np.array_equal(ids, rids)
+    _assert_same_state(net, o, "dt %g" % dt)
+    assert np.allclose(net.bw(), o.bw_state(), rtol=1e-12, atol=1e-15)
+    net.close()

@@ -156,3 +156,28 @@ def test_random_stream_through_a_tight_pool():
     for i, (g, p, n, seed, nid, _) in enumerate(reqs):
         _check(srv, ids[i], _alone(g, p, n, seed, nid))
     srv.close()
+
+
+def test_two_weight_requests_share_a_four_channel_pool():
+    """A server created with four accumulator channels serves one-weight and
+    two-weight requests together, each equal to its run alone; a server
+    without them refuses a two-weight request at submission."""
+    from paper_2211_15963_gb300 import dbnet
+    (g, p) = _request(40, 2600, 2, 90)
+    (h, q) = _request(41, 3100, 3, 110)
+    h = synth.with_second_weight(h, 42)
+    srv = dbnet.Server(max_neurons=1 << 14, max_requests=4, max_regions=16, max_delay=60,
+                       chunk_steps=128, arena_bytes=512 << 20, run=RUN, two_weights=1)
+    a = srv.submit(g, p, 1200, seed=9, net_id=1, raster_capacity=1 << 20)
+    srv.pump()
+    b = srv.submit(h, q, 900, seed=10, net_id=2, raster_capacity=1 << 20)
+    srv.drain()
+    _check(srv, a, _alone(g, p, 1200, 9, 1))
+    _check(srv, b, _alone(h, q, 900, 10, 2))
+    srv.close()
+    plain = dbnet.Server(max_neurons=1 << 13, max_requests=2, max_regions=8, max_delay=60,
+                         chunk_steps=64, arena_bytes=256 << 20, run=RUN)
+    with pytest.raises(dbnet.DbnetError) as ei:
+        plain.submit(h, q, 100, seed=1)
+    assert ei.value.code == dbnet.DBNET_EUNSUPPORTED
+    plain.close()
