@@ -184,6 +184,13 @@ const char* dbnet_strerror(int code);
 /* Detail of the last failure on the calling thread (static per thread). */
 const char* dbnet_last_error(void);
 
+/* sizeof of the public structs, for bindings to check their layouts:
+ * out[0..10] = dbnet_graph_t, dbnet_region_params_t, dbnet_options_t,
+ * dbnet_stats_t, dbens_enkf_t, dbnet_device_graph_t, dbsrv_options_t,
+ * dbsrv_request_t, dbsrv_status_t, dbsrv_stats_t, 0 (reserved).  Writes
+ * min(n, 11) entries; returns the number of structs (10).  Needs no GPU. */
+int dbnet_abi_sizes(int64_t* out, int n);
+
 /* Fill *o with the defaults: dt 0.1 ms, bin 1 ms, TR 800 ms, z_scale 1,
  * the standard hemodynamic constants, seed 1, net_id 0, automatic S,
  * precision 32, no raster, 4096 BOLD samples, autotune at step 2000. */

@@ -812,6 +812,19 @@ const char* dbnet_strerror(int code) {
 
 const char* dbnet_last_error(void) { return g_last_error.c_str(); }
 
+int dbnet_abi_sizes(int64_t* out, int n) {
+  const int64_t sz[11] = {
+      (int64_t)sizeof(dbnet_graph_t),   (int64_t)sizeof(dbnet_region_params_t),
+      (int64_t)sizeof(dbnet_options_t), (int64_t)sizeof(dbnet_stats_t),
+      (int64_t)sizeof(dbens_enkf_t),    (int64_t)sizeof(dbnet_device_graph_t),
+      (int64_t)sizeof(dbsrv_options_t), (int64_t)sizeof(dbsrv_request_t),
+      (int64_t)sizeof(dbsrv_status_t),  (int64_t)sizeof(dbsrv_stats_t),
+      0};
+  if (!out && n > 0) return DBNET_EINVAL;
+  for (int k = 0; k < n && k < 11; ++k) out[k] = sz[k];
+  return 10;
+}
+
 int dbnet_options_default(dbnet_options_t* o) {
   if (!o) return DBNET_EINVAL;
   std::memset(o, 0, sizeof(*o));

@@ -111,6 +111,7 @@ DBENS_T_NONE = -1
 _SIGS = {
     "dbnet_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dbnet_last_error": (ctypes.c_char_p, []),
+    "dbnet_abi_sizes": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dbnet_options_default": (ctypes.c_int, [ctypes.POINTER(dbnet_options_t)]),
     "dbnet_create": (ctypes.c_int, [ctypes.POINTER(dbnet_graph_t), _vp,
                                     ctypes.POINTER(dbnet_options_t), _vp, ctypes.POINTER(_vp)]),
@@ -172,6 +173,18 @@ def lib():
                 f.argtypes = args
             _lib = L
     return _lib
+
+
+ABI_STRUCTS = ("dbnet_graph_t", "dbnet_region_params_t", "dbnet_options_t", "dbnet_stats_t",
+               "dbens_enkf_t", "dbnet_device_graph_t", "dbsrv_options_t", "dbsrv_request_t",
+               "dbsrv_status_t", "dbsrv_stats_t")
+
+
+def abi_sizes() -> dict:
+    """sizeof of each public struct as the library was compiled, by name."""
+    out = np.zeros(11, dtype=np.int64)
+    n = lib().dbnet_abi_sizes(out.ctypes.data, len(out))
+    return dict(zip(ABI_STRUCTS[:n], (int(x) for x in out[:n])))
 
 
 class DbnetError(RuntimeError):

@@ -146,3 +146,13 @@ def test_enkf_targets_are_validated(lib):
             dbnet.ens_create(g, p, 3, th, {}, dbnet.enkf_options(target=tgt))
         assert ei.value.code == dbnet.DBNET_EINVAL, tgt
     _expect(dbnet.DBNET_EINVAL, g, synth.default_region_params(iext_shape=-1.0))
+
+
+def test_struct_layouts_match_the_library(lib):
+    """Every ctypes mirror has the size the C compiler gave the struct (a
+    field added on one side only shifts everything after it)."""
+    import ctypes
+    sizes = dbnet.abi_sizes()
+    assert set(sizes) == set(dbnet.ABI_STRUCTS)
+    for name, size in sizes.items():
+        assert ctypes.sizeof(getattr(dbnet, name)) == size, name
