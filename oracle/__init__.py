@@ -54,7 +54,7 @@ class OgGraph(ctypes.Structure):
                 ("region_offsets", ctypes.c_void_p), ("n_exc", ctypes.c_void_p),
                 ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
                 ("w_bf16", ctypes.c_void_p), ("delay", ctypes.c_void_p),
-                ("w2_bf16", ctypes.c_void_p)]
+                ("w2_bf16", ctypes.c_void_p), ("w_f64", ctypes.c_void_p)]
 
 
 class OgRegion(ctypes.Structure):
@@ -172,7 +172,8 @@ class Sim:
     """One network simulated by the oracle."""
 
     def __init__(self, graph, region_params, *, dt_ms=0.1, bin_ms=1.0, tr_ms=800.0,
-                 z_scale=1.0, bw=None, seed=1, net_id=0, fixed_shift=0, precision=32):
+                 z_scale=1.0, bw=None, seed=1, net_id=0, fixed_shift=0, precision=32,
+                 weights_f64=None):
         from synth import BW_DEFAULT
         bw = dict(BW_DEFAULT if bw is None else bw)
         if isinstance(region_params, dict):
@@ -182,9 +183,14 @@ class Sim:
         self._regs = (OgRegion * graph.n_regions)(*[region_struct(p) for p in region_params])
         w2 = getattr(graph, "w2_bf16", None)
         w2 = _addr(w2) if w2 is not None else None
+        wf = None
+        if weights_f64 is not None:   # unrounded first weights, [E]
+            self._wf = np.ascontiguousarray(weights_f64, dtype=np.float64)
+            assert len(self._wf) == graph.n_edges
+            wf = _addr(self._wf)
         g = OgGraph(graph.n_neurons, graph.n_regions, _addr(graph.region_offsets),
                     _addr(graph.n_exc), _addr(graph.row_ptr), _addr(graph.col),
-                    _addr(graph.w_bf16), _addr(graph.delay), w2)
+                    _addr(graph.w_bf16), _addr(graph.delay), w2, wf)
         o = OgOptions(dt_ms, bin_ms, tr_ms, z_scale, bw["kappa"], bw["gamma"], bw["tau"],
                       bw["alpha"], bw["rho"], bw["V0"], seed, net_id, fixed_shift, precision)
         err = ctypes.c_int(0)

@@ -36,6 +36,10 @@
 //     drive then adds w_ext to both AMPA and NMDA, as it adds to E in the
 //     one-weight form.
 //   * Accumulators hold fixed point: q(w) = rint(w * 2^S).
+//   * Weights are the BF16 values the device stores.  Optionally the first
+//     weight is an unrounded FP64 value instead (still accumulated as
+//     rint(w * 2^S), an absolute error of at most 2^-(S+1)), which states
+//     what the BF16 rounding of the weights costs.
 //   * Background: K_ext independent Poisson sources of rate nu per neuron,
 //     each adding w_ext to the E class; the count per step is drawn by integer
 //     inversion of one 32-bit Philox word against FP64 Poisson CDF thresholds.
@@ -120,6 +124,7 @@ struct OgGraph {
   const uint16_t* w_bf16;         // [E]
   const uint8_t* delay;           // [E] steps >= 1
   const uint16_t* w2_bf16;        // [E] second channel's weight, or NULL (one weight)
+  const double* w_f64;            // [E] unrounded first weight, or NULL (w_bf16 is used)
 };
 
 struct OgRegion {  // units: mV, ms, nF, uS, nA
@@ -272,7 +277,8 @@ struct Sim : SimBase {
     int32_t c = class_of(j);
     for (int64_t e = g.row_ptr[j]; e < g.row_ptr[j + 1]; ++e) {
       int64_t slot = (step_n + g.delay[e]) % D;
-      int64_t q = (int64_t)std::lrint(std::ldexp(bf16_value(g.w_bf16[e]), S));
+      double w = g.w_f64 ? g.w_f64[e] : bf16_value(g.w_bf16[e]);
+      int64_t q = (int64_t)std::lrint(std::ldexp(w, S));
       if (nch == 2) {
         ring[(size_t)((slot * N + g.col[e]) * 2 + c)] += q;
       } else {
@@ -418,7 +424,7 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
   std::vector<int32_t> indeg((size_t)N, 0);
   for (int64_t e = 0; e < g->row_ptr[N]; ++e) {
     dmax = g->delay[e] > dmax ? g->delay[e] : dmax;
-    double w = bf16_value(g->w_bf16[e]);
+    double w = g->w_f64 ? g->w_f64[e] : bf16_value(g->w_bf16[e]);
     wmax = w > wmax ? w : wmax;
     if (g->w2_bf16) {
       double w2 = bf16_value(g->w2_bf16[e]);
