@@ -38,7 +38,8 @@ extern "C" {
 #define DBNET_EINVAL (-1)      /* malformed graph, parameters or arguments */
 #define DBNET_ENOMEM (-2)      /* device or host allocation failed */
 #define DBNET_ECUDA (-3)       /* a CUDA runtime call failed */
-#define DBNET_ETIMEOUT (-4)    /* a bounded device wait gave up */
+#define DBNET_ETIMEOUT (-4)    /* reserved: no kernel of this library waits on
+                                  the device (each step is two plain launches) */
 #define DBNET_EOVERFLOW (-5)   /* fixed-point accumulation could overflow int32 */
 #define DBNET_ESTATE (-6)      /* handle poisoned by an earlier failure */
 #define DBNET_ERANGE (-7)      /* a caller buffer or a fixed capacity is too small */

@@ -744,11 +744,6 @@ void Engine::sync() {
   CK(cudaStreamSynchronize(stream));
   unsigned f = 0;
   CK(cudaMemcpy(&f, flags.p, sizeof(f), cudaMemcpyDeviceToHost));
-  if (f & kFlagWaitTimeout) {
-    poisoned = true;
-    poison_msg = "a bounded device wait gave up (state copy did not arrive)";
-    raise(DBNET_ETIMEOUT, poison_msg);
-  }
   if (f & kFlagHistOverflow)
     raise(DBNET_ERANGE, "spike ring overflowed its capacity");
 }

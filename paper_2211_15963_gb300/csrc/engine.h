@@ -150,9 +150,7 @@ struct StepRef {
 };
 
 enum : unsigned {
-  kFlagHistOverflow = 1u,
-  kFlagBoldOverflow = 2u,
-  kFlagWaitTimeout = 4u,  // a bounded device wait gave up (bulk copy not arrived)
+  kFlagHistOverflow = 1u,  // a spike did not fit its ring slot (cannot happen: a slot holds every neuron)
 };
 
 struct EngineDev {

@@ -337,7 +337,6 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     CK(cudaMemcpyAsync(&ev, at(kOffEvents), sizeof(ev), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&flags, at(kOffFlags), sizeof(flags), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (flags & kFlagWaitTimeout) raise(DBNET_ETIMEOUT, "a bounded device wait gave up");
     if (flags & kFlagHistOverflow) raise(DBNET_ERANGE, "spike ring overflowed");
     *n_spikes = (int64_t)out_dyn.spikes;
     *n_events = (int64_t)ev;
