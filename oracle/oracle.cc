@@ -8,7 +8,8 @@
 //     the capacitance-voltage equation and Eq. 2; Supplementary Sec. 3,
 //     "Numerical method", Eqs. 3 and 5 with the refractory reset);
 //   * push-based spike delivery (Supplementary Algorithm 2) into a ring of
-//     per-delay integer accumulators, indexed [slot][neuron][class];
+//     per-delay integer accumulators, indexed [slot][neuron][class] (or
+//     [slot][neuron][channel] with two weights per edge);
 //   * Poisson background input (Extended Data Table 2, "Input");
 //   * per-region spike counts and the Balloon-Windkessel BOLD model
 //     (Extended Data Table 4), integrated by forward Euler in FP64.

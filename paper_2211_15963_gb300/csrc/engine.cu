@@ -3,11 +3,12 @@
 // Create: host-side checks that cost O(N + R), then the edge arrays are
 // copied to the device in chunks of rows, each chunk validated by one
 // warp-per-row kernel (target range, delay range and order, weights -> BF16,
-// in-degrees, largest weight) that writes the interleaved edge records and
-// the per-delay segment table of its rows, the fixed-point scale is chosen
-// from those, the region
-// constants are derived in FP64 and rounded to FP32 once, and the initial
-// state is drawn on the device.
+// in-degrees, largest weight) that writes the interleaved edge records (6
+// bytes, or 8 with a second weight) and the per-delay segment table of its
+// rows; the fixed-point scale is chosen from those, the region constants are
+// derived in FP64 and rounded to FP32 once, and the initial state is drawn
+// on the device.  A graph with two weights per edge makes the engine keep
+// four accumulator channels per neuron.
 //
 // Step: (deliver, update) kernel pairs on the handle's stream, replayed from
 // a captured CUDA graph of kChunk steps; all per-step indices live in device
