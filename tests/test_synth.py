@@ -2,6 +2,8 @@
 (Extended Data Table 2): fixed in-degree, uniform sources without autapses
 or multapses, 4:1 E/I, cross-region sources excitatory, rows sorted by
 (delay, target)."""
+import os
+
 import numpy as np
 
 import synth
@@ -99,3 +101,22 @@ def test_cortical_columns_follow_the_population_counts():
     deg = np.diff(rp)
     assert deg.max() > 3 * np.median(deg)
     assert abs(len(tgt) / g.n_neurons - 200) < 10
+
+
+def test_generator_holds_only_its_output():
+    """The generator needs no per-edge memory beyond its output (7 bytes per
+    edge: target, BF16 weight, delay), so a 2e10-edge graph fits in 140 GB
+    of host memory.  Peak resident memory of a fresh process generating
+    2e8 edges, against its output plus a fixed allowance."""
+    import subprocess
+    import sys
+    code = ("import resource, synth\n"
+            "g = synth.make_graph([10000] * 20, 1000, 3, k_within=800, d_within=(1, 50),"
+            " d_cross=(50, 200))\n"
+            "print(g.n_edges, resource.getrusage(resource.RUSAGE_SELF).ru_maxrss)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                         timeout=600, check=True).stdout.split()
+    E, peak_kb = int(out[0]), int(out[1])
+    assert E == 200_000_000
+    assert peak_kb * 1024 < 7 * E + (600 << 20)
