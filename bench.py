@@ -91,10 +91,11 @@ def parse_from(argv):
 def workload_config(args, rank_count):
     two = getattr(args, "two_weights", False)
     rs = getattr(args, "region_size", 20000)
-    return {"workload": "%s network: %d neurons, %d regions x %d, in-degree %d, "
+    return {"workload": "%s network: %s neurons, %d regions x %s, in-degree %s, "
                         "dt 0.1 ms, ~%d Hz%s" % ("mid-size" if args.regions * rs <= 2_000_000 else "large",
-                                                  args.regions * rs, args.regions, rs, args.k_in,
-                                                  args.rate, ", two weights per edge" if two else ""),
+                                                  f"{args.regions * rs:,}", args.regions, f"{rs:,}",
+                                                  f"{args.k_in:,}", args.rate,
+                                                  ", two weights per edge" if two else ""),
             "weights_per_edge": 2 if two else 1,
             "neurons": args.regions * rs, "regions": args.regions, "in_degree": args.k_in,
             "dt_ms": 0.1, "target_rate_hz": args.rate, "step": "1 biological second",
