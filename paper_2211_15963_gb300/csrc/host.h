@@ -12,6 +12,7 @@
 
 #include "dbnet.h"
 #include "engine.h"
+#include "freelist.h"
 
 namespace dbn {
 
@@ -55,44 +56,21 @@ class Arena {
                 cudaGetErrorString(e));
     }
     size_ = bytes;
-    free_.clear();
-    free_[0] = bytes;
+    free_.reset(bytes);
   }
   void* take(int64_t bytes) {
     bytes = round(bytes);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      const int64_t off = it->first, len = it->second;
-      free_.erase(it);
-      if (len > bytes) free_[off + bytes] = len - bytes;
-      used_ += bytes;
-      return base_ + off;
-    }
-    return nullptr;
+    const int64_t off = free_.take(bytes);
+    if (off < 0) return nullptr;
+    used_ += bytes;
+    return base_ + off;
   }
   void give(void* p, int64_t bytes) {
     bytes = round(bytes);
-    int64_t off = static_cast<char*>(p) - base_;
     used_ -= bytes;
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && off + bytes == nx->first) {
-      bytes += nx->second;
-      nx = free_.erase(nx);
-    }
-    if (nx != free_.begin()) {
-      auto pv = std::prev(nx);
-      if (pv->first + pv->second == off) {
-        pv->second += bytes;
-        return;
-      }
-    }
-    free_[off] = bytes;
+    free_.give(static_cast<char*>(p) - base_, bytes);
   }
-  int64_t largest_free() const {
-    int64_t m = 0;
-    for (const auto& kv : free_) m = kv.second > m ? kv.second : m;
-    return m;
-  }
+  int64_t largest_free() const { return free_.largest(); }
   int64_t used() const { return used_; }
   int64_t size() const { return size_; }
   static int64_t round(int64_t b) { return (b + 255) / 256 * 256; }
@@ -100,7 +78,7 @@ class Arena {
  private:
   char* base_ = nullptr;
   int64_t size_ = 0, used_ = 0;
-  std::map<int64_t, int64_t> free_;  // offset -> length
+  FreeList<int64_t> free_;  // byte offsets
 };
 
 // The arena DevBuf::alloc draws from on this thread (nullptr: cudaMalloc).

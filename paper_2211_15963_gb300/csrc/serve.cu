@@ -45,48 +45,6 @@ double now_s() {
   return std::chrono::duration<double>(clk::now().time_since_epoch()).count();
 }
 
-// First-fit allocator over a range of integer units (tiles, region slots).
-class RangePool {
- public:
-  void init(int32_t n) {
-    free_.clear();
-    if (n > 0) free_[0] = n;
-  }
-  int32_t take(int32_t n) {
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < n) continue;
-      const int32_t at = it->first, len = it->second;
-      free_.erase(it);
-      if (len > n) free_[at + n] = len - n;
-      return at;
-    }
-    return -1;
-  }
-  bool fits(int32_t n) const {
-    for (const auto& kv : free_)
-      if (kv.second >= n) return true;
-    return false;
-  }
-  void give(int32_t at, int32_t n) {
-    auto nx = free_.lower_bound(at);
-    if (nx != free_.end() && at + n == nx->first) {
-      n += nx->second;
-      nx = free_.erase(nx);
-    }
-    if (nx != free_.begin()) {
-      auto pv = std::prev(nx);
-      if (pv->first + pv->second == at) {
-        pv->second += n;
-        return;
-      }
-    }
-    free_[at] = n;
-  }
-
- private:
-  std::map<int32_t, int32_t> free_;  // start -> length
-};
-
 struct Req {
   int64_t id = 0;
   dbnet_graph_t graph{};                       // caller's host arrays (until admitted)
@@ -126,7 +84,7 @@ struct dbsrv {
   std::map<int64_t, std::unique_ptr<dbn::Req>> reqs;
   std::deque<int64_t> queue;
   std::vector<dbn::Slot> slots;
-  dbn::RangePool tiles, regions;
+  dbn::FreeList<int32_t> tiles, regions;  // first fit over tiles and region slots
   std::map<uint64_t, std::weak_ptr<dbn::GraphDev>> shared;
   std::deque<dbn::Round> rounds;
   std::vector<cudaEvent_t> spare;
@@ -457,8 +415,8 @@ int dbsrv_create(const dbsrv_options_t* options, void* cuda_stream, dbsrv_t** ou
     s->arena.init(o.arena_bytes);
     CK(cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking));
     s->slots.assign((size_t)o.max_requests, Slot{});
-    s->tiles.init((int32_t)tiles);
-    s->regions.init(o.max_regions);
+    s->tiles.reset((int32_t)tiles);
+    s->regions.reset(o.max_regions);
     CK(cudaStreamSynchronize(s->eng->stream));
   });
   if (rc == DBNET_OK) *out = s.release();
