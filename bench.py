@@ -74,7 +74,7 @@ def parse_from(argv):
     ap.add_argument("--two-weights", action="store_true",
                     help="mid workload with a second weight per edge (four accumulator channels)")
     ap.add_argument("--workload", default="mid",
-                    choices=["mid", "ensemble", "serving", "nest", "columns", "dt-study"],
+                    choices=["mid", "ensemble", "serving", "nest", "columns", "dt-study", "small"],
                     help="mid: the headline line; ensemble: 64-member HMDA ensemble (steps = "
                          "TRs) against one network per launch; serving: request stream")
     ap.add_argument("--members", type=int, default=64)
@@ -788,6 +788,64 @@ def run_nest(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ small network ----
+def run_small(args):
+    """The 10,000-neuron network (one region, in-degree 100, delays 1-20
+    steps, 10 Hz Poisson drive per neuron).  Its working set (~2 MB of state,
+    6 MB of edges) stays in the L2, so the step is bound by launch and
+    kernel latency, and the figures are microseconds per step and the
+    real-time factor rather than a fraction of HBM bandwidth."""
+    import torch
+    import synth
+    import __graft_entry__
+    from paper_2211_15963_gb300 import dbnet
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    g = synth.small_network()
+    p = synth.default_region_params()
+    net = dbnet.Network(g, p, dict(seed=synth.seed_for(0) + 1), stream)
+    for _ in range(args.warmup):
+        net.step(STEPS_PER_BIO_S)
+    net.sync()
+    s0 = net.stats()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        net.step(STEPS_PER_BIO_S)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    s1 = net.stats()
+    t_del, t_upd = net.step_timed(args.profile_steps)
+    net.close()
+    n_steps = STEPS_PER_BIO_S * args.steps
+    line = {
+        "metric": "microseconds per Euler step", "value": 1e3 * ms / n_steps, "unit": "us/step",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators, f64 BOLD",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": "small network: 10,000 neurons (8,000 E / 2,000 I), one region, "
+                               "in-degree 100, delays 1-20 steps, dt 0.1 ms, 10 Hz drive",
+                   "step": "1 biological second (10,000 Euler steps)",
+                   "l2": "resident (the whole working set fits in the L2)"},
+        "rtf": ms / args.steps / 1e3,
+        "events_per_s": (s1["events"] - s0["events"]) / (ms * 1e-3),
+        "mean_rate_hz": (s1["spikes"] - s0["spikes"]) / g.n_neurons / args.steps,
+        "kernels_us": {"k_deliver": 1e3 * t_del / args.profile_steps,
+                       "k_update": 1e3 * t_upd / args.profile_steps},
+        "clocks": clk, "gpu_launches": 2 * n_steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------- step-size accuracy study ----
 DT_STUDY_MS = (1.0, 0.5, 0.2, 0.1, 0.05, 0.02, 0.01, 0.008)   # the last is the reference
 DT_STUDY_STEPS = 1000   # 1 ms samples of V: one biological second
@@ -1025,6 +1083,8 @@ def main():
         run_columns(args)
     elif args.workload == "dt-study":
         run_dt_study(args)
+    elif args.workload == "small":
+        run_small(args)
     else:
         run_ours(args)
 
