@@ -585,3 +585,128 @@ def test_heterogeneous_current_enters_the_membrane_bracket():
     expect = V0 + (0.1 / p["C"]) * (-p["gL"] * (V0 - p["VL"]) + p["I_ext"] * f)
     assert np.allclose(s.state()[0], expect, rtol=1e-13, atol=1e-12)
     assert f.std() > 0.1  # the factors differ between neurons
+
+
+# ------------------------------------------- bins, z and the BOLD samples ----
+def _isolated_spike_steps(k, n_ref, m0, T):
+    """Spike steps of an isolated neuron under constant current that starts at
+    V_reset with m0 refractory steps left: it is clamped for m0 steps, then
+    needs k free steps to cross (the closed form of the ISI pin above), so it
+    fires at m0 + k - 1 and every n_ref + k steps after."""
+    return list(range(m0 + k - 1, T, n_ref + k))
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_bin_counts_z_and_bold_samples_follow_the_spike_schedule(precision):
+    """Fig. 2a and Extended Data Table 4: at the end of every bin of spb
+    steps, z_r = z_scale x (spikes of region r in that bin) / N_r drives one
+    Euler step of the hemodynamic model, the count restarts from zero, and
+    the BOLD value after every bins_per_tr-th bin is sampled.  Regions of
+    different sizes and currents, a bin of 5 steps and a TR of 7 bins (not
+    a multiple of any spike period): the spike schedule comes from the
+    closed-form ISI, the hemodynamic steps from the pinned bw_step, so a
+    count divided by N instead of N_r, a count that is not reset, or a bin
+    or TR index off by one fails."""
+    sizes = [3, 5, 2, 6]
+    currents = [0.6, 0.75, 0.9, 0.68]
+    dt, bin_ms, tr_ms, z_scale = 0.1, 0.5, 3.5, 3.0
+    spb, bins_per_tr = 5, 7
+    N, R = sum(sizes), len(sizes)
+    g = synth.graph_from_dense(np.zeros((N, N)), np.ones((N, N), dtype=np.int64), sizes, 0.5)
+    params = [synth.default_region_params(I_ext=I, drive_rate_hz=0.0, g_u=(0.0, 0.0, 0.0, 0.0))
+              for I in currents]
+    rng = np.random.default_rng(11)
+    m0 = rng.integers(0, 40, N).astype(np.int32)
+    T = 2 * spb * bins_per_tr * 13 + 17  # ends inside a bin
+    s = oracle.Sim(g, params, dt_ms=dt, bin_ms=bin_ms, tr_ms=tr_ms, z_scale=z_scale,
+                   precision=precision)
+    s.set_state(V=np.full(N, params[0]["Vreset"]), J=np.zeros((4, N)), ref=m0)
+    s.step(T)
+    ro = np.asarray(g.region_offsets)
+    counts = np.zeros((T // spb + 1, R), dtype=np.int64)
+    spikes = []
+    for r in range(R):
+        p = params[r]
+        a = 1.0 - dt * p["gL"] / p["C"]
+        Vinf = p["VL"] + p["I_ext"] / p["gL"]
+        kstar = math.log((Vinf - p["Vth"]) / (Vinf - p["Vreset"])) / math.log(a)
+        assert 0.05 < kstar - math.floor(kstar) < 0.95  # away from a rounding tie
+        k, n_ref = math.ceil(kstar), round(p["Tref"] / dt)
+        for i in range(ro[r], ro[r + 1]):
+            for n in _isolated_spike_steps(k, n_ref, int(m0[i]), T):
+                counts[n // spb, r] += 1
+                spikes.append((n, i))
+    st, ids = s.raster()
+    assert sorted(spikes) == sorted(zip(st.tolist(), ids.tolist()))
+    x = np.tile(np.array([0.0, 1.0, 1.0, 1.0]), (R, 1))
+    bold = []
+    n_bins = T // spb
+    for b in range(n_bins):
+        y = np.zeros(R)
+        for r in range(R):
+            z = z_scale * float(counts[b, r]) / float(sizes[r])
+            xr = x[r].copy()
+            y[r] = oracle.bw_step(xr, z, bin_ms * 1e-3, synth.BW_DEFAULT)
+            x[r] = xr
+        if (b + 1) % bins_per_tr == 0:
+            bold.append(y)
+    got = s.bold()
+    assert got.shape == (n_bins // bins_per_tr, R) and len(bold) == got.shape[0] > 10
+    assert np.array_equal(got, np.array(bold))
+    assert np.array_equal(s.bw_state(), x)
+    # the partial last bin is still counting
+    assert np.array_equal(s.counts(), counts[n_bins])
+    assert s.info()["bins_done"] == n_bins
+
+
+# ------------------------------------------- EnKF state helpers (Sec. 6) ----
+def test_pack_and_unpack_state_follow_the_region_block_layout():
+    """Supplementary Sec. 6: the state of a member holds, per region, the
+    hyperparameters and the hemodynamic state with its BOLD value.  The
+    block of region r is [theta_AMPA, theta_GABA_A, s, f, v, q, y], written
+    out by hand here for two members and two regions."""
+    theta = np.array([[[0.1, 0.2], [0.3, 0.4]], [[-0.1, -0.2], [-0.3, -0.4]]])
+    bw = np.array([[[1.0, 1.1, 1.2, 1.3], [2.0, 2.1, 2.2, 2.3]],
+                   [[3.0, 3.1, 3.2, 3.3], [4.0, 4.1, 4.2, 4.3]]])
+    y = np.array([[0.01, 0.02], [0.03, 0.04]])
+    X = enkf.pack_state(theta, bw, y)
+    expect = np.array([
+        [0.1, 0.2, 1.0, 1.1, 1.2, 1.3, 0.01, 0.3, 0.4, 2.0, 2.1, 2.2, 2.3, 0.02],
+        [-0.1, -0.2, 3.0, 3.1, 3.2, 3.3, 0.03, -0.3, -0.4, 4.0, 4.1, 4.2, 4.3, 0.04],
+    ])
+    assert np.array_equal(X, expect)
+    th2, bw2, y2 = enkf.unpack_state(expect)
+    assert np.array_equal(th2, theta) and np.array_equal(bw2, bw) and np.array_equal(y2, y)
+    # the named positions agree with the layout
+    assert enkf.BLOCK == 7 and enkf.Y_INDEX == 6 and enkf.THETA == (0, 1)
+
+
+def test_constrain_clips_hyperparameters_and_floors_flow_volume_q():
+    """After an analysis the log scales go back into the prior support
+    [theta_lo, theta_hi] and f, v, q are kept at or above the floor; s and y
+    are left as they are.  Expected values written out by hand."""
+    lo, hi, floor = -0.5, 0.5, 0.01
+    X = np.array([
+        [0.7, -0.9, -0.3, 0.005, -1.0, 0.02, -0.04, 0.2, -0.5, 0.1, 1.5, 0.01, -2.0, 0.3],
+        [-0.5, 0.5, 0.4, 2.0, 0.0, 0.009, 0.05, 1e3, -1e3, -0.2, 0.011, 0.5, 0.0099, -0.1],
+    ])
+    expect = np.array([
+        [0.5, -0.5, -0.3, 0.01, 0.01, 0.02, -0.04, 0.2, -0.5, 0.1, 1.5, 0.01, 0.01, 0.3],
+        [-0.5, 0.5, 0.4, 2.0, 0.01, 0.01, 0.05, 0.5, -0.5, -0.2, 0.011, 0.5, 0.01, -0.1],
+    ])
+    got = enkf.constrain(X, lo, hi, floor)
+    assert np.array_equal(got, expect)
+    assert np.array_equal(X[0, :2], [0.7, -0.9])  # the input is not modified
+
+
+def test_random_walk_moves_only_the_hyperparameters_and_clips():
+    """Supplementary Sec. 6: theta(t) = theta(t - 1) + eps_theta with eps_theta
+    = rw_sigma x xi, clipped to the prior support; nothing else moves.
+    Expected values written out by hand (rw_sigma = 0.5)."""
+    lo, hi = -1.0, 1.0
+    X = np.array([[0.2, -0.8, 9.0, 9.1, 9.2, 9.3, 9.4, 0.9, 0.0, 8.0, 8.1, 8.2, 8.3, 8.4]])
+    xi = np.array([[[1.0, -1.0], [0.4, 0.6]]])   # [M=1, R=2, 2]
+    expect = np.array([[0.7, -1.0, 9.0, 9.1, 9.2, 9.3, 9.4, 1.0, 0.3, 8.0, 8.1, 8.2, 8.3, 8.4]])
+    got = enkf.random_walk(X, 0.5, xi, lo, hi)
+    assert np.allclose(got, expect, rtol=0, atol=1e-15)
+    assert np.array_equal(got[:, 2:7], X[:, 2:7]) and np.array_equal(got[:, 9:], X[:, 9:])
