@@ -302,7 +302,11 @@ int ens_step(dbens_t* h, int64_t n_steps);
  * sample, then the random walk of theta and the rescaling of the members'
  * conductances.  eps_obs [M][R] and xi_rw [M][R][2] are standard-normal draws
  * (NULL: drawn on the device from Philox).  y_pred_mean [R] (may be NULL)
- * receives the forecast ensemble mean of y before the analysis. */
+ * receives the forecast ensemble mean of y before the analysis.
+ * DBNET_EINVAL for a non-finite y_obs, eps_obs or xi_rw (checked on the
+ * host) and for an analysis that fails on the device (a covariance that is
+ * not positive definite, or a non-finite analysed state); a failed analysis
+ * leaves theta, the hemodynamic state and the members' constants unchanged. */
 int ens_assimilate(dbens_t* h, const double* y_obs, const double* eps_obs,
                    const double* xi_rw, double* y_pred_mean);
 
@@ -344,7 +348,10 @@ void ens_destroy(dbens_t* h);
  * larger inputs return DBNET_ERANGE.
  * Set-up: the first call on each device looks up the scratch address with
  * cudaGetSymbolAddress while that device is current; make that first call
- * before any stream capture.  The call waits for its work to finish.
+ * before any stream capture.  The address is kept for the life of the
+ * process, so the library must not be used across a cudaDeviceReset (or any
+ * other destruction of the device's primary context).  The call waits for
+ * its work to finish.
  * Every call reuses the same scratch and clears it first, so calls that
  * overlap on the GPU (from several threads or streams) race. */
 #define DBNET_NOALLOC_MAX_NEURONS 65536

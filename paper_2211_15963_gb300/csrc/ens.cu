@@ -176,10 +176,24 @@ __global__ void k_apply_global(double* X, const double* Z, const double* nu, int
   X[i] += s;
 }
 
+// Sets bit 2 of *bad when the analysed ensemble holds a non-finite value
+// (for instance a forecast whose hemodynamic state overflowed).
+__global__ void k_check_finite(const double* X, int64_t n, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(X[i])) {
+      atomicOr(bad, 2);
+      return;
+    }
+}
+
+// The two kernels that write the members' state do nothing when the
+// analysis failed (*bad != 0), so a failed call leaves theta, the
+// hemodynamic state and the region constants as they were.
 __global__ void k_constrain_writeback(const double* X, double* theta, double* bw, int M, int R,
-                                      double lo, double hi, double floor_) {
+                                      double lo, double hi, double floor_, const int* bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M * R) return;
+  if (i >= M * R || *bad) return;
   const int m = i / R, r = i % R;
   const double* x = X + (size_t)m * kB * R + kB * r;
   theta[2 * i] = fmin(fmax(x[0], lo), hi);
@@ -226,9 +240,9 @@ __device__ __forceinline__ void set_target(RegionConst& rc, int target, float v)
 
 __global__ void k_walk_rescale(double* theta, const double* xi, const double* base_g,
                                const InstDesc* insts, int M, int R, double rw, double lo,
-                               double hi, int t0, int t1) {
+                               double hi, int t0, int t1, const int* bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M * R) return;
+  if (i >= M * R || *bad) return;
   const int m = i / R, r = i % R;
   const double ta = fmin(fmax(theta[2 * i] + rw * xi[2 * i], lo), hi);
   const double tg = fmin(fmax(theta[2 * i + 1] + rw * xi[2 * i + 1], lo), hi);
@@ -406,6 +420,10 @@ int ens_assimilate(dbens_t* h, const double* y_obs, const double* eps_obs, const
     const int M = h->M, R = h->R, n = kB * R;
     for (int r = 0; r < R; ++r)
       if (!std::isfinite(y_obs[r])) raise(DBNET_EINVAL, "non-finite observation");
+    for (int64_t i = 0; eps_obs && i < (int64_t)M * R; ++i)
+      if (!std::isfinite(eps_obs[i])) raise(DBNET_EINVAL, "non-finite observation perturbation");
+    for (int64_t i = 0; xi_rw && i < (int64_t)M * R * 2; ++i)
+      if (!std::isfinite(xi_rw[i])) raise(DBNET_EINVAL, "non-finite random-walk draw");
     cudaStream_t s = e.stream;
     CK(cudaMemcpyAsync(h->yobs.p, y_obs, sizeof(double) * R, cudaMemcpyHostToDevice, s));
     if (eps_obs)
@@ -430,12 +448,13 @@ int ens_assimilate(dbens_t* h, const double* y_obs, const double* eps_obs, const
       k_chol_solve<<<blocks(n), 128, 0, s>>>(h->S.p, h->P.p, R, n);
       k_apply_global<<<blocks(M * n), 128, 0, s>>>(h->X.p, h->P.p, h->nu.p, M, R);
     }
+    k_check_finite<<<blocks((int64_t)M * n), 128, 0, s>>>(h->X.p, (int64_t)M * n, h->bad.p);
     k_constrain_writeback<<<blocks(M * R), 128, 0, s>>>(h->X.p, h->theta.p, e.bw.p, M, R,
                                                          h->enkf.theta_lo, h->enkf.theta_hi,
-                                                         h->enkf.floor);
+                                                         h->enkf.floor, h->bad.p);
     k_walk_rescale<<<blocks(M * R), 128, 0, s>>>(h->theta.p, h->xi.p, h->base_g.p, e.desc.p, M, R,
                                                   h->enkf.rw_sigma, h->enkf.theta_lo, h->enkf.theta_hi,
-                                                  h->target[0], h->target[1]);
+                                                  h->target[0], h->target[1], h->bad.p);
     CK(cudaGetLastError());
     int bad = 0;
     CK(cudaMemcpyAsync(&bad, h->bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -446,7 +465,8 @@ int ens_assimilate(dbens_t* h, const double* y_obs, const double* eps_obs, const
     }
     CK(cudaStreamSynchronize(s));
     h->n_analyses += 1;
-    if (bad) raise(DBNET_EINVAL, "observation covariance is not positive definite");
+    if (bad & 1) raise(DBNET_EINVAL, "observation covariance is not positive definite; members unchanged");
+    if (bad) raise(DBNET_EINVAL, "the analysis produced a non-finite state; members unchanged");
     if (y_pred_mean)
       for (int r = 0; r < R; ++r) y_pred_mean[r] = mu[(size_t)(kB * r + kY)];
   });

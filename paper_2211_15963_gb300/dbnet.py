@@ -440,31 +440,91 @@ class Network:
 
 
 # ------------------------------------------------------- allocation-free ----
+def noalloc_check(n_neurons, region_offsets, n_exc, row_ptr, col, weight_bf16, delay, V, J, ref,
+                  raster_step=None, raster_id=None, n_edges=None):
+    """Argument checks of dbnet_run_noalloc that the C side cannot make (it
+    sees bare device pointers): every tensor is contiguous CUDA memory on the
+    current device with the dtype and at least the element count the
+    kernels index -- row_ptr int64 [N+1]; col int32, weight_bf16 int16 or
+    uint16 and delay uint8 with n_edges elements each; V float32 [n_pad];
+    J float32 [4 n_pad]; ref uint8 [n_pad]; raster_step and raster_id int32
+    of equal length -- where n_pad = ceil(N / 1024) x 1024, and
+    region_offsets has one entry more than n_exc.  Raises ValueError on the
+    first mismatch.  `n_edges` is row_ptr[N] (read from the device by the
+    caller).  Touches no GPU."""
+    N = int(n_neurons)
+    if N < 1:
+        raise ValueError("n_neurons must be >= 1")
+    if len(region_offsets) != len(n_exc) + 1:
+        raise ValueError("region_offsets needs len(n_exc) + 1 entries")
+    n_pad = (N + 1023) // 1024 * 1024
+    cur = _current_device()
+
+    def need(name, t, dtypes, count):
+        if t is None:
+            raise ValueError("%s is required" % name)
+        if not (getattr(t, "is_cuda", False) and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA tensor" % name)
+        if cur is not None and t.device.index != cur:
+            raise ValueError("%s is on cuda:%s, not the current device cuda:%d" % (name, t.device.index, cur))
+        if str(t.dtype) not in dtypes:
+            raise ValueError("%s must be %s, not %s" % (name, " or ".join(dtypes), t.dtype))
+        if t.numel() < count:
+            raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), count))
+
+    need("row_ptr", row_ptr, ("torch.int64",), N + 1)
+    E = 0 if n_edges is None else int(n_edges)
+    need("col", col, ("torch.int32",), E)
+    need("weight_bf16", weight_bf16, ("torch.int16", "torch.uint16", "torch.bfloat16"), E)
+    need("delay", delay, ("torch.uint8",), E)
+    need("V", V, ("torch.float32",), n_pad)
+    need("J", J, ("torch.float32",), 4 * n_pad)
+    need("ref", ref, ("torch.uint8",), n_pad)
+    if (raster_step is None) != (raster_id is None):
+        raise ValueError("raster_step and raster_id go together")
+    if raster_step is not None:
+        need("raster_step", raster_step, ("torch.int32",), 0)
+        need("raster_id", raster_id, ("torch.int32",), raster_step.numel())
+        if raster_id.numel() != raster_step.numel():
+            raise ValueError("raster_step and raster_id must have the same length")
+
+
+def _current_device():
+    try:
+        import torch
+        return torch.cuda.current_device() if torch.cuda.is_available() else None
+    except Exception:  # noqa: BLE001
+        return None
+
+
 def dbnet_run_noalloc(n_neurons, region_offsets, n_exc, row_ptr, col, weight_bf16, delay, params,
                       options, n_steps, V, J, ref, raster_step=None, raster_id=None, stream=None):
     """Run through the allocation-free entry point.  row_ptr, col,
     weight_bf16, delay, V [n_pad], J [4, n_pad], ref [n_pad] (uint8) and the
     optional raster buffers are CUDA tensors the caller allocated;
-    region_offsets and n_exc are host arrays.  Returns (n_spikes, n_events)."""
-    def dptr(t):
-        if t is None:
-            return 0
-        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
-            raise ValueError("expected a contiguous CUDA tensor")
-        return int(t.data_ptr())
+    region_offsets and n_exc are host arrays.  Every tensor is checked
+    (noalloc_check) before the call.  Returns (n_spikes, n_events)."""
     ro = np.ascontiguousarray(region_offsets, dtype=np.int32)
     ne = np.ascontiguousarray(n_exc, dtype=np.int32)
+    n_edges = None
+    if getattr(row_ptr, "is_cuda", False) and row_ptr.numel() >= int(n_neurons) + 1:
+        n_edges = int(row_ptr[int(n_neurons)].item())   # one 8-byte read of the caller's row_ptr
+    noalloc_check(n_neurons, ro, ne, row_ptr, col, weight_bf16, delay, V, J, ref, raster_step,
+                  raster_id, n_edges)
     R = len(ne)
-    g = dbnet_device_graph_t(int(n_neurons), R, ro.ctypes.data, ne.ctypes.data, dptr(row_ptr),
-                             dptr(col), dptr(weight_bf16), dptr(delay))
+    g = dbnet_device_graph_t(int(n_neurons), R, ro.ctypes.data, ne.ctypes.data,
+                             int(row_ptr.data_ptr()), int(col.data_ptr()),
+                             int(weight_bf16.data_ptr()), int(delay.data_ptr()))
     P = params_array(params, R)
     o = options_from(options)
     cap = 0 if raster_step is None else int(raster_step.numel())
+    rs = 0 if raster_step is None else int(raster_step.data_ptr())
+    ri = 0 if raster_id is None else int(raster_id.data_ptr())
     ns, ne_ = _i64(0), _i64(0)
     _check(lib().dbnet_run_noalloc(ctypes.byref(g), ctypes.cast(P, _vp), ctypes.byref(o),
-                                   int(n_steps), dptr(V), dptr(J), dptr(ref), dptr(raster_step),
-                                   dptr(raster_id), cap, ctypes.byref(ns), ctypes.byref(ne_),
-                                   _stream(stream)), "dbnet_run_noalloc")
+                                   int(n_steps), int(V.data_ptr()), int(J.data_ptr()),
+                                   int(ref.data_ptr()), rs, ri, cap, ctypes.byref(ns),
+                                   ctypes.byref(ne_), _stream(stream)), "dbnet_run_noalloc")
     return ns.value, ne_.value
 
 

@@ -156,3 +156,72 @@ def test_struct_layouts_match_the_library(lib):
     assert set(sizes) == set(dbnet.ABI_STRUCTS)
     for name, size in sizes.items():
         assert ctypes.sizeof(getattr(dbnet, name)) == size, name
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor in the wrapper's argument checks (no GPU
+    here, and the checks read only metadata)."""
+
+    def __init__(self, dtype, n, device=0, contiguous=True, cuda=True):
+        self.dtype, self._n, self._contig, self.is_cuda = dtype, n, contiguous, cuda
+
+        class _D:
+            index = device
+        self.device = _D()
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._contig
+
+
+def _noalloc_args(N=3000, E=9000):
+    import torch
+    n_pad = (N + 1023) // 1024 * 1024
+    F = _FakeCudaTensor
+    return dict(n_neurons=N, region_offsets=[0, 1000, N], n_exc=[800, 1600],
+                row_ptr=F(torch.int64, N + 1), col=F(torch.int32, E), weight_bf16=F(torch.int16, E),
+                delay=F(torch.uint8, E), V=F(torch.float32, n_pad), J=F(torch.float32, 4 * n_pad),
+                ref=F(torch.uint8, n_pad), raster_step=F(torch.int32, 100),
+                raster_id=F(torch.int32, 100), n_edges=E)
+
+
+def test_noalloc_wrapper_rejects_mismatched_tensors_without_touching_a_gpu(monkeypatch):
+    """dbnet_run_noalloc receives bare device pointers, so its binding checks
+    dtype, length, contiguity and device of every tensor first; none of
+    these cases reaches the library."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(dbnet, "_current_device", lambda: 0)
+    F = _FakeCudaTensor
+    dbnet.noalloc_check(**_noalloc_args())  # the well-formed case passes
+    n_pad = 3072
+    bad = {
+        "row_ptr": F(torch.int32, 3001),             # int32 row pointers
+        "col": F(torch.int32, 8999),                 # one edge short
+        "weight_bf16": F(torch.float32, 9000),       # float weights
+        "delay": F(torch.int32, 9000),               # wide delays
+        "V": F(torch.float32, 3000),                 # not padded to whole tiles
+        "J": F(torch.float32, 3 * n_pad),            # three channels
+        "ref": F(torch.int32, n_pad),                # wide refractory counters
+        "raster_id": F(torch.int32, 99),             # shorter than raster_step
+    }
+    for name, t in bad.items():
+        a = _noalloc_args()
+        a[name] = t
+        with pytest.raises(ValueError):
+            dbnet.noalloc_check(**a)
+    for t in (F(torch.float32, n_pad, device=1), F(torch.float32, n_pad, contiguous=False),
+              F(torch.float32, n_pad, cuda=False)):
+        a = _noalloc_args()
+        a["V"] = t
+        with pytest.raises(ValueError):
+            dbnet.noalloc_check(**a)
+    a = _noalloc_args()
+    a["region_offsets"] = [0, 3000]                 # one entry short for two regions
+    with pytest.raises(ValueError):
+        dbnet.noalloc_check(**a)
+    a = _noalloc_args()
+    a["raster_id"] = None
+    with pytest.raises(ValueError):
+        dbnet.noalloc_check(**a)

@@ -234,3 +234,47 @@ def test_task_twin_experiment_recovers_injected_current():
     assert abs(th[:, :, 0].mean() - np.log(1.5)) < abs(start - np.log(1.5))
     hidden.close()
     ens.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_failed_analysis_leaves_members_unchanged(mode):
+    """An analysis whose forecast is not finite is refused (DBNET_EINVAL) and
+    changes nothing: theta, the hemodynamic state and the members' region
+    constants stay as they were.  A huge z_scale overflows every region's
+    hemodynamic state within a few bins (FP64 overflow, not a fault); a later
+    analysis on a healthy ensemble still runs."""
+    from paper_2211_15963_gb300 import dbnet
+    g = _graph()
+    base = [synth.default_region_params(I_ext=0.9) for _ in range(g.n_regions)]
+    M = 4
+    theta = np.random.default_rng(3).uniform(LO, HI, (M, g.n_regions, 2))
+    opts = dict(seed=9, net_id=300, tr_ms=10.0, z_scale=1e300)
+    ens = dbnet.Ensemble(g, base, M, theta, opts, dict(mode=mode, obs_var=1e-6))
+    ens.step(400)
+    th0, bw0, y0 = ens.read()
+    assert not np.all(np.isfinite(bw0))   # the forecast is broken
+    with pytest.raises(dbnet.DbnetError) as ei:
+        ens.assimilate(np.zeros(g.n_regions))
+    assert ei.value.code == dbnet.DBNET_EINVAL and "unchanged" in str(ei.value)
+    th1, bw1, y1 = ens.read()
+    assert np.array_equal(th1, th0)
+    assert np.array_equal(bw1, bw0, equal_nan=True)
+    # the members' conductances were not rescaled: a member still equals a
+    # single network with its initial scales
+    ens.step(100)
+    net = dbnet.Network(g, _member_params(base, theta[1]), dict(opts, net_id=301))
+    net.step(500)
+    a, b = ens.member_state(1), net.state()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    net.close()
+    ens.close()
+    # non-finite caller draws are refused on the host
+    ens = dbnet.Ensemble(g, base, M, theta, dict(opts, z_scale=1.0), dict(mode=mode))
+    ens.step(100)
+    eps = np.zeros((M, g.n_regions))
+    eps[2, 1] = np.nan
+    with pytest.raises(dbnet.DbnetError):
+        ens.assimilate(np.zeros(g.n_regions), eps_obs=eps)
+    ens.assimilate(np.zeros(g.n_regions), eps_obs=np.zeros((M, g.n_regions)))
+    ens.close()
