@@ -44,7 +44,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         tmp = _SO + ".tmp%d" % os.getpid()
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, src])
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, src])
         os.replace(tmp, _SO)
     return _SO
 
@@ -75,7 +75,8 @@ class OgOptions(ctypes.Structure):
                 ("bw_tau", ctypes.c_double), ("bw_alpha", ctypes.c_double),
                 ("bw_rho", ctypes.c_double), ("bw_V0", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("net_id", ctypes.c_uint64),
-                ("fixed_shift", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("fixed_shift", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("bin_spikes", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def lib():
@@ -89,6 +90,7 @@ def lib():
             L.og_create.argtypes = [ctypes.POINTER(OgGraph), vp, ctypes.POINTER(OgOptions),
                                     ctypes.POINTER(ctypes.c_int)]
             L.og_destroy.argtypes = [vp]
+            L.og_set_threads.argtypes = [vp, i32]
             L.og_step.argtypes = [vp, i64]
             L.og_deliver_only.argtypes = [vp, vp, i64, i64]
             L.og_read_state.argtypes = [vp, vp, vp, vp]
@@ -173,7 +175,7 @@ class Sim:
 
     def __init__(self, graph, region_params, *, dt_ms=0.1, bin_ms=1.0, tr_ms=800.0,
                  z_scale=1.0, bw=None, seed=1, net_id=0, fixed_shift=0, precision=32,
-                 weights_f64=None):
+                 weights_f64=None, bin_spikes=False, threads=1):
         from synth import BW_DEFAULT
         bw = dict(BW_DEFAULT if bw is None else bw)
         if isinstance(region_params, dict):
@@ -192,7 +194,8 @@ class Sim:
                     _addr(graph.n_exc), _addr(graph.row_ptr), _addr(graph.col),
                     _addr(graph.w_bf16), _addr(graph.delay), w2, wf)
         o = OgOptions(dt_ms, bin_ms, tr_ms, z_scale, bw["kappa"], bw["gamma"], bw["tau"],
-                      bw["alpha"], bw["rho"], bw["V0"], seed, net_id, fixed_shift, precision)
+                      bw["alpha"], bw["rho"], bw["V0"], seed, net_id, fixed_shift, precision,
+                      1 if bin_spikes else 0, 0)
         err = ctypes.c_int(0)
         self._h = lib().og_create(ctypes.byref(g), ctypes.cast(self._regs, ctypes.c_void_p),
                                   ctypes.byref(o), ctypes.byref(err))
@@ -200,6 +203,17 @@ class Sim:
             raise ValueError("oracle rejected the network (code %d)" % err.value)
         self.N = graph.n_neurons
         self.R = graph.n_regions
+        if threads != 1:
+            self.set_threads(threads)
+
+    def set_threads(self, n: int) -> None:
+        """Threads of the timing variant (OpenMP; 0 = every core).  The
+        results do not depend on it: neuron ranges are joined in order and
+        the accumulators are exact integers."""
+        if n <= 0:
+            n = os.cpu_count() or 1
+        self.threads = int(n)
+        lib().og_set_threads(self._h, self.threads)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -64,6 +64,8 @@
 //     stream 5 (attempt a uses counter (0, i, 5, a): word 0 a Box-Muller
 //     normal, word 1 the acceptance uniform, word 2 for k < 1 the uniform of
 //     G(k) = G(k + 1) U^(1/k)), in FP64, rounded once to the state type.
+#include <omp.h>
+
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -142,6 +144,8 @@ struct OgOptions {
   uint64_t seed, net_id;
   int32_t fixed_shift;  // 0 = automatic
   int32_t precision;    // 32 = matched FP32, 64 = FP64
+  int32_t bin_spikes;   // 1: spikes are handed on at the end of their bin
+  int32_t pad;
 };
 
 void og_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
@@ -247,7 +251,10 @@ struct SimBase {
   // shared bookkeeping
   int32_t N = 0, R = 0, D = 0, S = 0, spb = 0, bins_per_tr = 0;
   int32_t nch = 2;  // accumulator channels: 2 classes, or 4 with two weights per edge
+  int32_t threads = 1;  // > 1: the timing variant (OpenMP), same results
+  int32_t bin_spikes = 0;
   int64_t n = 0, events = 0, spikes = 0, bins_done = 0;
+  std::vector<int64_t> last_release;  // with bin_spikes: release step of each neuron's last spike
   std::vector<int64_t> ring;  // [D][N][nch]
   std::vector<int32_t> raster_step, raster_id;
   std::vector<int32_t> region_of, cnt;
@@ -274,25 +281,132 @@ struct Sim : SimBase {
   // Supplementary Algorithm 2, the push of a spike's synaptic input: every
   // out-edge of spiker j adds q(w) to the accumulator slot its delay selects
   // (with two weights: q(w) to channel 2c and q(w2) to channel 2c + 1).
-  void scatter(int32_t j, int64_t step_n) {
+  // (The threaded timing variant adds with atomic integer additions: the sums
+  // are exact, so their order does not matter.)
+  static void add(int64_t& a, int64_t q, bool atomic) {
+    if (atomic) __atomic_fetch_add(&a, q, __ATOMIC_RELAXED);
+    else a += q;
+  }
+  int64_t scatter(int32_t j, int64_t step_n, bool atomic = false) {
     int32_t c = class_of(j);
+    int64_t ev = 0;
     for (int64_t e = g.row_ptr[j]; e < g.row_ptr[j + 1]; ++e) {
       int64_t slot = (step_n + g.delay[e]) % D;
       double w = g.w_f64 ? g.w_f64[e] : bf16_value(g.w_bf16[e]);
       int64_t q = (int64_t)std::lrint(std::ldexp(w, S));
       if (nch == 2) {
-        ring[(size_t)((slot * N + g.col[e]) * 2 + c)] += q;
+        add(ring[(size_t)((slot * N + g.col[e]) * 2 + c)], q, atomic);
       } else {
         int64_t q2 = (int64_t)std::lrint(std::ldexp(bf16_value(g.w2_bf16[e]), S));
-        ring[(size_t)((slot * N + g.col[e]) * 4 + 2 * c)] += q;
-        ring[(size_t)((slot * N + g.col[e]) * 4 + 2 * c + 1)] += q2;
+        add(ring[(size_t)((slot * N + g.col[e]) * 4 + 2 * c)], q, atomic);
+        add(ring[(size_t)((slot * N + g.col[e]) * 4 + 2 * c + 1)], q2, atomic);
       }
-      ++events;
+      ++ev;
     }
+    return ev;
+  }
+
+  // The step at which a spike of step m is handed on.  Without binning it
+  // is m itself.  With binning (Supplementary Sec. 3, "Numerical method": the
+  // accumulated spike A_j(t) is non-zero only at bin edges t = k b_t and
+  // then counts the spikes of (t - b_t, t]) a spike emitted in a step of the
+  // bin [k spb, (k + 1) spb) takes effect as if emitted in the bin's last
+  // step, so that an edge of delay d reaches the accumulator consumed at
+  // step (k + 1) spb - 1 + d: with d = 1, the first step of the next bin.
+  int64_t release_step(int64_t m) const {
+    return bin_spikes ? (m / spb + 1) * spb - 1 : m;
+  }
+
+  // The spikes of one step, in neuron order: each is handed on to its
+  // targets (once per bin with binning: A_j is an indicator).
+  void deliver_fired(const std::vector<int32_t>& fired, int64_t step_n) {
+    const int64_t rel = release_step(step_n);
+    std::vector<int32_t> go;
+    go.reserve(fired.size());
+    for (int32_t j : fired) {
+      if (bin_spikes) {
+        if (last_release[(size_t)j] == rel) continue;
+        last_release[(size_t)j] = rel;
+      }
+      go.push_back(j);
+    }
+    if (threads <= 1) {
+      for (int32_t j : go) events += scatter(j, rel);
+      return;
+    }
+    int64_t ev = 0;
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 16) reduction(+ : ev)
+    for (int64_t k = 0; k < (int64_t)go.size(); ++k) ev += scatter(go[(size_t)k], rel, true);
+    events += ev;
   }
 
   void deliver_only(const int32_t* ids, int64_t count, int64_t step_n) override {
-    for (int64_t k = 0; k < count; ++k) scatter(ids[k], step_n);
+    for (int64_t k = 0; k < count; ++k) events += scatter(ids[k], step_n);
+  }
+
+  // One neuron's step (the order of operations the matched-FP32 oracle fixes).
+  void update_neuron(int32_t i, int64_t slot, Real inv2S, std::vector<int32_t>& fired) {
+    const RegionConst<Real>& p = rc[(size_t)region_of[(size_t)i]];
+    // this step's arrivals per channel (AMPA, NMDA, GABA_A, GABA_B): in
+    // the one-weight form both channels of a class read its class sum
+    int64_t* a = &ring[(size_t)((slot * N + i) * nch)];
+    int64_t ach[4];
+    for (int u4 = 0; u4 < 4; ++u4) ach[u4] = nch == 2 ? a[u4 / 2] : a[u4];
+    for (int k = 0; k < nch; ++k) a[k] = 0;
+    // background Poisson count by integer inversion
+    uint32_t u = (uint32_t)(neuron_word(o.seed, o.net_id, (uint64_t)n, i, 0) >> 32);
+    int64_t c = 0;
+    for (int32_t k = 0; k < p.n_thr; ++k) c += (u >= p.thr[k]) ? 1 : 0;
+    ach[0] += c * (int64_t)p.q_ext;
+    ach[1] += c * (int64_t)p.q_ext;
+    // membrane (Eq. 5, bracket times dt/C) with the old V and J
+    Real v = V[(size_t)i];
+    Real Isyn = (Real)0;
+    for (int u4 = 0; u4 < 4; ++u4) {
+      Real gj = p.g[u4] * J[(size_t)u4 * N + i];
+      Real dv = p.Vu[u4] - v;
+      Real t = gj * dv;
+      Isyn = Isyn + t;
+    }
+    Real leak = p.gL * (v - p.VL);
+    Real I = Isyn - leak;
+    if (p.het) {
+      Real ie = p.Iext * fext[(size_t)i];
+      I = I + ie;
+    } else {
+      I = I + p.Iext;
+    }
+    if (p.ou_on) I = I + Ibg[(size_t)i];
+    Real dV = I * p.dtC;
+    Real vn = v + dV;
+    // background current (Eq. 1, Euler-Maruyama) after its use above
+    if (p.ou_on) {
+      Real& ib = Ibg[(size_t)i];
+      const Real xi = (Real)box_muller(neuron_word(o.seed, o.net_id, (uint64_t)n, i, 4));
+      Real dI = p.ou_mu - ib;
+      Real t1 = dI * p.ou_k;
+      ib = ib + t1;
+      Real t2 = p.ou_s * xi;
+      ib = ib + t2;
+    }
+    // synaptic traces (Eq. 3): decay, then this step's arrivals
+    for (int u4 = 0; u4 < 4; ++u4) {
+      Real x = (Real)ach[u4] * inv2S;
+      Real& j = J[(size_t)u4 * N + i];
+      Real d = p.dec[u4] * j;
+      j = d + x;
+    }
+    // refractory clamp, threshold and reset
+    if (ref[(size_t)i] > 0) {
+      V[(size_t)i] = p.Vreset;
+      ref[(size_t)i] -= 1;
+    } else if (vn >= p.Vth) {
+      V[(size_t)i] = p.Vreset;
+      ref[(size_t)i] = p.n_ref;
+      fired.push_back(i);
+    } else {
+      V[(size_t)i] = vn;
+    }
   }
 
   void step(int64_t n_steps) override {
@@ -300,71 +414,23 @@ struct Sim : SimBase {
     for (int64_t it = 0; it < n_steps; ++it, ++n) {
       const int64_t slot = n % D;
       std::vector<int32_t> fired;
-      for (int32_t i = 0; i < N; ++i) {
-        const RegionConst<Real>& p = rc[(size_t)region_of[(size_t)i]];
-        // this step's arrivals per channel (AMPA, NMDA, GABA_A, GABA_B): in
-        // the one-weight form both channels of a class read its class sum
-        int64_t* a = &ring[(size_t)((slot * N + i) * nch)];
-        int64_t ach[4];
-        for (int u4 = 0; u4 < 4; ++u4) ach[u4] = nch == 2 ? a[u4 / 2] : a[u4];
-        for (int k = 0; k < nch; ++k) a[k] = 0;
-        // background Poisson count by integer inversion
-        uint32_t u = (uint32_t)(neuron_word(o.seed, o.net_id, (uint64_t)n, i, 0) >> 32);
-        int64_t c = 0;
-        for (int32_t k = 0; k < p.n_thr; ++k) c += (u >= p.thr[k]) ? 1 : 0;
-        ach[0] += c * (int64_t)p.q_ext;
-        ach[1] += c * (int64_t)p.q_ext;
-        // membrane (Eq. 5, bracket times dt/C) with the old V and J
-        Real v = V[(size_t)i];
-        Real Isyn = (Real)0;
-        for (int u4 = 0; u4 < 4; ++u4) {
-          Real gj = p.g[u4] * J[(size_t)u4 * N + i];
-          Real dv = p.Vu[u4] - v;
-          Real t = gj * dv;
-          Isyn = Isyn + t;
+      if (threads <= 1) {
+        for (int32_t i = 0; i < N; ++i) update_neuron(i, slot, inv2S, fired);
+      } else {
+        // timing variant: contiguous neuron ranges per thread, their spike
+        // lists joined in neuron order (the same list as the loop above)
+        std::vector<std::vector<int32_t>> part((size_t)threads);
+#pragma omp parallel num_threads(threads)
+        {
+          const int t = omp_get_thread_num();
+          const int32_t lo = (int32_t)((int64_t)N * t / threads);
+          const int32_t hi = (int32_t)((int64_t)N * (t + 1) / threads);
+          for (int32_t i = lo; i < hi; ++i) update_neuron(i, slot, inv2S, part[(size_t)t]);
         }
-        Real leak = p.gL * (v - p.VL);
-        Real I = Isyn - leak;
-        if (p.het) {
-          Real ie = p.Iext * fext[(size_t)i];
-          I = I + ie;
-        } else {
-          I = I + p.Iext;
-        }
-        if (p.ou_on) I = I + Ibg[(size_t)i];
-        Real dV = I * p.dtC;
-        Real vn = v + dV;
-        // background current (Eq. 1, Euler-Maruyama) after its use above
-        if (p.ou_on) {
-          Real& ib = Ibg[(size_t)i];
-          const Real xi = (Real)box_muller(neuron_word(o.seed, o.net_id, (uint64_t)n, i, 4));
-          Real dI = p.ou_mu - ib;
-          Real t1 = dI * p.ou_k;
-          ib = ib + t1;
-          Real t2 = p.ou_s * xi;
-          ib = ib + t2;
-        }
-        // synaptic traces (Eq. 3): decay, then this step's arrivals
-        for (int u4 = 0; u4 < 4; ++u4) {
-          Real x = (Real)ach[u4] * inv2S;
-          Real& j = J[(size_t)u4 * N + i];
-          Real d = p.dec[u4] * j;
-          j = d + x;
-        }
-        // refractory clamp, threshold and reset
-        if (ref[(size_t)i] > 0) {
-          V[(size_t)i] = p.Vreset;
-          ref[(size_t)i] -= 1;
-        } else if (vn >= p.Vth) {
-          V[(size_t)i] = p.Vreset;
-          ref[(size_t)i] = p.n_ref;
-          fired.push_back(i);
-        } else {
-          V[(size_t)i] = vn;
-        }
+        for (auto& v : part) fired.insert(fired.end(), v.begin(), v.end());
       }
+      deliver_fired(fired, n);
       for (int32_t j : fired) {
-        scatter(j, n);
         raster_step.push_back((int32_t)n);
         raster_id.push_back(j);
         cnt[(size_t)region_of[(size_t)j]] += 1;
@@ -434,7 +500,10 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
     indeg[(size_t)g->col[e]] += 1;
   }
   for (int32_t i = 0; i < N; ++i) kin_max = indeg[(size_t)i] > kin_max ? indeg[(size_t)i] : kin_max;
-  s->D = dmax + 1;
+  // with binning a spike waits up to spb - 1 steps for its bin to end
+  const int32_t spb = (int32_t)std::lrint(o->bin_ms / o->dt_ms);
+  s->bin_spikes = o->bin_spikes ? 1 : 0;
+  s->D = dmax + 1 + (s->bin_spikes && spb > 1 ? spb - 1 : 0);
   double wext_max = 0.0;
   for (int32_t r = 0; r < R; ++r) wext_max = regs[r].w_ext > wext_max ? regs[r].w_ext : wext_max;
   // fixed-point scale: 2^S, S = 16 unless the worst-case sum of one step's
@@ -506,6 +575,7 @@ SimBase* make_sim(const OgGraph* g, const OgRegion* regs, const OgOptions* o, in
   }
   s->nch = g->w2_bf16 ? 4 : 2;
   s->ring.assign((size_t)s->D * N * s->nch, 0);
+  if (s->bin_spikes) s->last_release.assign((size_t)N, -1);
   s->cnt.assign((size_t)R, 0);
   s->bw.resize((size_t)R * 4);
   for (int32_t r = 0; r < R; ++r) {
@@ -534,6 +604,8 @@ void* og_create(const OgGraph* g, const OgRegion* regs, const OgOptions* o, int*
 }
 
 void og_destroy(void* h) { delete (SimBase*)h; }
+// Threads of the timing variant (1 = the plain loop; results are identical).
+void og_set_threads(void* h, int32_t n) { ((SimBase*)h)->threads = n > 1 ? n : 1; }
 void og_step(void* h, int64_t n) { ((SimBase*)h)->step(n); }
 void og_deliver_only(void* h, const int32_t* ids, int64_t count, int64_t n) {
   ((SimBase*)h)->deliver_only(ids, count, n);

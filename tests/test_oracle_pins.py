@@ -710,3 +710,91 @@ def test_random_walk_moves_only_the_hyperparameters_and_clips():
     got = enkf.random_walk(X, 0.5, xi, lo, hi)
     assert np.allclose(got, expect, rtol=0, atol=1e-15)
     assert np.array_equal(got[:, 2:7], X[:, 2:7]) and np.array_equal(got[:, 9:], X[:, 9:])
+
+
+# ------------------------------------------------ spike binning (b_t) -------
+@pytest.mark.parametrize("spb,dt", [(5, 0.1), (10, 0.1), (1, 0.1), (2, 0.5)])
+def test_binned_delivery_matches_brute_force(spb, dt):
+    """Supplementary Sec. 3, "Numerical method": with a spike bin b_t the
+    accumulated spike A_j(t) is non-zero only at bin edges t = k b_t, where it
+    marks a spike of j in (t - b_t, t]; Eq. 3 then adds w A_j(t).  So a spike
+    emitted in any step of bin [k spb, (k + 1) spb) acts as if emitted in the
+    bin's last step and reaches, over an edge of delay d, the accumulator
+    consumed at step (k + 1) spb - 1 + d; a neuron that fires twice in one bin
+    counts once.  Isolated sources (one of them fast enough to fire twice in
+    a bin) drive silent targets over random delays; after every step the
+    pending accumulators must equal the brute-force sum over the raster's
+    spikes, edge by edge, exactly."""
+    n_src, n_tgt = 6, 9
+    N = n_src + n_tgt
+    rng = np.random.default_rng(spb)
+    W = np.zeros((N, N))
+    Dl = np.ones((N, N), dtype=np.int64)
+    W[n_src:, :n_src] = synth.bf16_to_f64(synth.f64_to_bf16(rng.lognormal(-1, 0.5, (n_tgt, n_src))))
+    Dl[n_src:, :n_src] = rng.integers(1, 13, (n_tgt, n_src))
+    W[n_src + 2, 0] = 0.0  # a missing edge
+    src = synth.default_region_params(I_ext=2.5, drive_rate_hz=0.0, Tref=2.0)
+    fast = dict(src, Tref=0.0, I_ext=12.0)
+    tgt = synth.default_region_params(I_ext=0.0, drive_rate_hz=0.0, g_u=(0.0, 0.0, 0.0, 0.0))
+    # regions: the fast source, the other sources, the targets (half E, half I each)
+    s = oracle.Sim(synth.graph_from_dense(W, Dl, [1, n_src - 1, n_tgt], 0.5), [fast, src, tgt],
+                   dt_ms=dt, bin_ms=spb * dt, tr_ms=spb * dt * 4, precision=64, bin_spikes=True)
+    g = s.graph
+    D = s.info()["D"]
+    S = s.info()["S"]
+    dmax = int(Dl[n_src:, :n_src].max())
+    assert D == dmax + spb
+    ro = np.asarray(g.region_offsets)
+    cls = np.zeros(N, dtype=np.int64)
+    for r in range(3):
+        cls[ro[r] + int(g.n_exc[r]):ro[r + 1]] = 1
+    rp, col = np.asarray(g.row_ptr), np.asarray(g.col)
+    wq = np.rint(np.ldexp(synth.bf16_to_f64(np.asarray(g.w_bf16)), S)).astype(np.int64)
+    dly = np.asarray(g.delay).astype(np.int64)
+    T = 40 * spb + 3
+    twice = False
+    for t in range(T):
+        s.step(1)
+        st, ids = s.raster()
+        seen = set()
+        want = np.zeros((D, N, 2), dtype=np.int64)
+        for m, j in zip(st.tolist(), ids.tolist()):
+            rel = (m // spb + 1) * spb - 1
+            if (j, rel) in seen:
+                twice = True
+                continue
+            seen.add((j, rel))
+            for e in range(rp[j], rp[j + 1]):
+                a = rel + dly[e]
+                if a >= t + 1:   # not yet consumed
+                    want[a % D, col[e], cls[j]] += wq[e]
+        assert np.array_equal(s.ring(), want), t
+        assert np.all(ids < n_src)   # the targets stay silent
+    assert len(st) > 20
+    assert twice == (spb > 1)       # the fast source fired twice within a bin
+    # with one step per bin, binning changes nothing
+    if spb == 1:
+        s0 = oracle.Sim(s.graph, [fast, src, tgt], dt_ms=dt, bin_ms=dt, tr_ms=dt * 4,
+                        precision=64)
+        s0.step(T)
+        assert np.array_equal(s0.raster()[1], s.raster()[1])
+        assert np.array_equal(s0.state()[1], s.state()[1])
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_threaded_timing_variant_gives_identical_results(small_graph, precision):
+    """The oracle's all-core timing variant (neuron ranges per thread, spike
+    lists joined in order, exact integer accumulation with atomic adds) gives
+    the single-threaded oracle's raster, state, accumulators and BOLD."""
+    p = synth.default_region_params()
+    a = oracle.Sim(small_graph, p, seed=5, tr_ms=20.0, precision=precision)
+    b = oracle.Sim(small_graph, p, seed=5, tr_ms=20.0, precision=precision, threads=4)
+    a.step(400)
+    b.step(400)
+    for x, y in zip(a.raster(), b.raster()):
+        assert np.array_equal(x, y)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.ring(), b.ring())
+    assert np.array_equal(a.bold(), b.bold())
+    assert a.info() == b.info() and a.info()["spikes"] > 500
