@@ -11,8 +11,10 @@ Functions and the passages they follow:
 * ``Sim``: conductance LIF update (Methods, capacitance-voltage equation and
   Eq. 2; Supplementary Sec. 3, Eqs. 3 and 5), push delivery into a per-delay
   ring (Supplementary Algorithm 2), Poisson background (Extended Data
-  Table 2), Balloon-Windkessel readout (Extended Data Table 4).  FP64 and
-  op-order-matched FP32 modes.
+  Table 2), Balloon-Windkessel readout (Extended Data Table 4), optional
+  spike binning (Supplementary Sec. 3, "Numerical method").  FP64 and
+  op-order-matched FP32 modes; an all-core timing variant (``threads``)
+  with identical results.
 * ``bw_step``: one forward-Euler step of Extended Data Table 4.
 * ``philox4x64``: Philox4x64-10 (Salmon et al., SC'11), the counter-based
   generator the drive draws from.

@@ -2,8 +2,11 @@
 // tests, the smoke check and the benchmark's CPU-baseline leg may call it; the
 // product (the CUDA library) never does, and the two share no code.
 //
-// It is a plain, slow, single-threaded restatement of the method, step by
-// step, in the order the paper gives it:
+// It is a plain, slow restatement of the method, step by step, in the order
+// the paper gives it (single-threaded; an optional timing variant, set by
+// og_set_threads, runs the neuron loop over contiguous ranges on several
+// threads and the delivery with atomic integer additions, with results
+// identical to the single-threaded loop):
 //   * conductance LIF neurons (Methods, "Simulating Digital Brain on GPUs",
 //     the capacitance-voltage equation and Eq. 2; Supplementary Sec. 3,
 //     "Numerical method", Eqs. 3 and 5 with the refractory reset);
@@ -37,6 +40,11 @@
 //     drive then adds w_ext to both AMPA and NMDA, as it adds to E in the
 //     one-weight form.
 //   * Accumulators hold fixed point: q(w) = rint(w * 2^S).
+//   * Optional spike binning (Supplementary Sec. 3, "Numerical method"): the
+//     accumulated spike A_j(t) is non-zero only at bin edges t = k b_t, where
+//     it marks a spike of j in (t - b_t, t].  A spike of any step of a bin is
+//     handed on as if emitted in the bin's last step; a neuron that fires
+//     twice in one bin is handed on once (A_j is 0 or 1).
 //   * Weights are the BF16 values the device stores.  Optionally the first
 //     weight is an unrounded FP64 value instead (still accumulated as
 //     rint(w * 2^S), an absolute error of at most 2^-(S+1)), which states
