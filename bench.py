@@ -1,21 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the Digital Brain hot path on one GB300 (or N replicas).
 
-Workload: the mid-size network -- 2,000,000 conductance LIF neurons in 100
-regions of 20,000 (80 % E / 20 % I), in-degree 1,000 (800 within the region,
-200 from excitatory neurons of other regions drawn from a seeded 100x100
-region matrix of density 0.3), BF16 lognormal weights, delays 0.1-5 ms within
-and 5-20 ms across regions, dt = 0.1 ms, drive tuned to ~7 / 15 / 30 Hz
-(--rate).  Synthetic, seeded.  One benchmark step = one biological second
+Headline workload (the default): the largest network one GPU holds --
+20,000,000 conductance LIF neurons in 200 regions of 100,000 (80 % E /
+20 % I), in-degree 1,000 (800 within the region, 200 from excitatory neurons
+of other regions drawn from a seeded 200x200 region matrix of density 0.3),
+2e10 synapses as 6-byte (target, BF16 weight) records (120 GB), delays
+0.1-5 ms within and 5-20 ms across regions, dt = 0.1 ms, drive tuned to
+~7 / 15 / 30 Hz (--rate).  Synthetic, seeded; the host graph (140 GB) is
+ingested from pageable memory.  One benchmark step = one biological second
 (10,000 Euler steps: update, compaction, delivery, region counts, BOLD).
 
 Metric: synaptic events per second (events applied to the accumulators,
 counted on the device).  Also reported: real-time factor (wall s per
 biological s), neuron updates/s, per-kernel roofline against the measured
-HBM copy bandwidth, the end-to-end figure through the C ABI from pinned host
-buffers, and the CPU oracle timed on the host cores.
+HBM copy bandwidth, the end-to-end figure through the C ABI from host
+buffers, the CPU oracle timed on the host cores, and compact lines for the
+mid-size network, the 10,000-neuron network, the batched HMDA ensemble and
+the request server (--no-extras skips them).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--rate 7|15|30]
+  python bench.py --workload mid|small|ensemble|serving|nest|columns|dt-study
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
 For N > 1, launch with torch.distributed.run; each rank runs an independent
 replica (the path does not shard: replicas only) and rank 0 prints.
@@ -42,13 +47,19 @@ STEPS_PER_BIO_S = 10_000  # dt = 0.1 ms
 # (5 regions of 20,000): 6.9, 14.7 and 29.4 Hz there.
 RATE_DRIVE = {7: 3.1757, 15: 7.2221, 30: 16.4246}
 UPDATE_BYTES_PER_NEURON = 58   # V r/w 8, J r/w 32, ref r/w 2, accumulator read + clear 16
-DELIVER_BYTES_PER_EVENT = 14   # target|delay 4 + BF16 weight 2 + int32 read-modify-write 8
+DELIVER_BYTES_PER_EVENT = 14   # target 4 + BF16 weight 2 + int32 read-modify-write 8
 # with two weights per edge: four accumulator channels (read + clear 32) and
 # 8-byte records (target 4 + two BF16 weights 4) with an int64 read-modify-write 16
 UPDATE_BYTES_PER_NEURON_FOUR = 74
 DELIVER_BYTES_PER_EVENT_TWO = 24
 METRIC = "synaptic events/s"
 UNIT = "events/s"
+# (regions, neurons per region) of the two network workloads
+WORKLOAD_DIMS = {"large": (200, 100_000), "mid": (100, 20_000)}
+# kernels launched per dbnet_step(10,000): 156 replays of the 64-step graph
+# (128 launches each) + 16 direct steps (2 each) + the graph's base word + the
+# bin close at the end of the call
+LAUNCHES_PER_BIO_S = 156 * 128 + 16 * 2 + 2
 
 
 def parse():
@@ -65,18 +76,25 @@ def parse_from(argv):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--profile-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--regions", type=int, default=100, help="regions of --region-size neurons")
-    ap.add_argument("--region-size", type=int, default=20000,
-                    help="neurons per region (the largest configuration: 200 x 100,000)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact mid/small/batched/served lines of the default run")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="threads of the oracle's timing variant (0 = every core)")
+    ap.add_argument("--regions", type=int, default=None, help="regions of --region-size neurons")
+    ap.add_argument("--region-size", type=int, default=None, help="neurons per region")
     ap.add_argument("--pageable", action="store_true",
-                    help="host graph in pageable memory (for graphs too large to pin)")
+                    help="host graph in pageable memory (always so for the large workload)")
     ap.add_argument("--k-in", type=int, default=1000, help="in-degree (80 %% within region)")
     ap.add_argument("--two-weights", action="store_true",
-                    help="mid workload with a second weight per edge (four accumulator channels)")
-    ap.add_argument("--workload", default="mid",
-                    choices=["mid", "ensemble", "serving", "nest", "columns", "dt-study", "small"],
-                    help="mid: the headline line; ensemble: 64-member HMDA ensemble (steps = "
-                         "TRs) against one network per launch; serving: request stream")
+                    help="a second weight per edge (four accumulator channels)")
+    ap.add_argument("--bin-spikes", action="store_true",
+                    help="hand spikes on at the 1 ms bin edges (Supplementary Sec. 3)")
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "mid", "ensemble", "serving", "nest", "columns", "dt-study",
+                             "small"],
+                    help="large: the headline line (20 M neurons); mid: 2 M neurons; ensemble: "
+                         "64-member HMDA ensemble (steps = TRs) against one network per launch; "
+                         "serving: request stream")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--separate-trs", type=int, default=1,
                     help="TRs timed for the one-network-per-launch comparison")
@@ -88,16 +106,27 @@ def parse_from(argv):
     return ap.parse_args(argv)
 
 
-def workload_config(args, rank_count):
+def workload_dims(args):
+    """(regions, neurons per region) of a network workload."""
+    R, S = WORKLOAD_DIMS.get(args.workload, WORKLOAD_DIMS["mid"])
+    return (args.regions or R), (args.region_size or S)
+
+
+def network_name(n):
+    return ("largest single-GPU network" if n >= 20_000_000 else
+            "mid-size network" if n >= 1_000_000 else "network")
+
+
+def workload_config(args, rank_count, dims=None):
     two = getattr(args, "two_weights", False)
-    rs = getattr(args, "region_size", 20000)
-    return {"workload": "%s network: %s neurons, %d regions x %s, in-degree %s, "
-                        "dt 0.1 ms, ~%d Hz%s" % ("mid-size" if args.regions * rs <= 2_000_000 else "large",
-                                                  f"{args.regions * rs:,}", args.regions, f"{rs:,}",
-                                                  f"{args.k_in:,}", args.rate,
-                                                  ", two weights per edge" if two else ""),
+    R, rs = dims or workload_dims(args)
+    n = R * rs
+    return {"workload": "%s: %s neurons, %d regions x %s, in-degree %s, dt 0.1 ms, ~%d Hz%s%s"
+                        % (network_name(n), f"{n:,}", R, f"{rs:,}", f"{args.k_in:,}", args.rate,
+                           ", two weights per edge" if two else "",
+                           ", spikes handed on at 1 ms bin edges" if getattr(args, "bin_spikes", False) else ""),
             "weights_per_edge": 2 if two else 1,
-            "neurons": args.regions * rs, "regions": args.regions, "in_degree": args.k_in,
+            "neurons": n, "regions": R, "in_degree": args.k_in, "synapses": n * args.k_in,
             "dt_ms": 0.1, "target_rate_hz": args.rate, "step": "1 biological second",
             "replicas": rank_count,
             "l2": "flushed (256 MiB write) between timed steps; edge arrays exceed L2"}
@@ -156,10 +185,11 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers ----
-def rank_seed(rank):
-    """Graph seed of replica `rank` (each rank simulates its own network)."""
+def rank_seed(rank, large=False):
+    """Graph seed of replica `rank` (each rank simulates its own network):
+    the largest network's recipe index 4, the mid-size network's 1."""
     import synth
-    return synth.seed_for(1) + 1000 * rank
+    return synth.seed_for(4 if large else 1) + 1000 * rank
 
 
 def combine_ranks(events, spikes, neurons, dev_ms, world, device):
@@ -220,16 +250,24 @@ def pinned_alloc(torch):
     return alloc, keep
 
 
-def oracle_sample(params, seconds=12.0):
-    """The CPU oracle (matched FP32, single thread) on a 1/20-scale sample of
-    the workload: 5 regions of 20,000 neurons, in-degree 1,000, same drive.
-    200 ms are simulated untimed to pass the onset transient, then whole
-    1 ms chunks are timed until `seconds` of CPU time have elapsed."""
+def oracle_sample(args, dims, seconds=15.0, onset_steps=500):
+    """The CPU oracle (matched FP32) on a bounded sample of a network
+    workload, on the host cores: a 1/20-scale network of the same region
+    size, in-degree and drive (a twentieth of the regions), run untimed
+    past the onset, then timed in 1 ms chunks for about `seconds` of wall
+    time.  The oracle runs its all-core timing variant (results identical to
+    the single-threaded loop) with --cpu-threads threads (0 = every core)."""
     import oracle
     import synth
-    g = synth.mid_network(n_regions=5, seed=synth.seed_for(1) + 100)
-    s = oracle.Sim(g, params, seed=synth.seed_for(1) + 1, precision=32)
-    s.step(2000)
+    R, S = dims
+    r_s = max(1, R // 20)
+    g = synth.make_graph([S] * r_s, args.k_in, synth.seed_for(1) + 100,
+                         k_within=int(round(0.8 * args.k_in)) if r_s > 1 else args.k_in,
+                         d_within=(1, 50), d_cross=(50, 200))
+    threads = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
+    s = oracle.Sim(g, params_for(args.rate, args.k_in), seed=synth.seed_for(1) + 1, precision=32,
+                   threads=threads)
+    s.step(onset_steps)
     i0 = s.info()
     t0 = time.perf_counter()
     steps = 0
@@ -239,63 +277,69 @@ def oracle_sample(params, seconds=12.0):
     wall = time.perf_counter() - t0
     i1 = s.info()
     ev = i1["events"] - i0["events"]
-    return {"value": ev / wall, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": ev / wall, "unit": UNIT, "cores": threads, "kind": "oracle",
             "neuron_updates_per_s": g.n_neurons * steps / wall,
-            "sample": "%d steps (%.0f ms biological) of a 100,000-neuron, in-degree-1,000 "
-                      "1/20-scale network after a 200 ms untimed onset; single-threaded "
-                      "matched-FP32 oracle" % (steps, steps * 0.1)}
+            "rtf_of_sample": wall / (steps * 1e-4),
+            "cpu": cpu_model(),
+            "sample": "%d Euler steps (%.0f ms biological) of a %s-neuron 1/20-scale network "
+                      "(%d regions x %s, in-degree %s, same drive) after %d untimed steps; the "
+                      "matched-FP32 oracle's all-core timing variant on %d threads"
+                      % (steps, steps * 0.1, f"{g.n_neurons:,}", r_s, f"{S:,}", f"{args.k_in:,}",
+                         onset_steps, threads)}
 
 
-# -------------------------------------------------------------- our arm ----
-def run_ours(args):
-    import numpy as np
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup, e2e_steps,
+                profile_steps, pageable, clocked=True):
+    """One network workload: generate, create, warm up, time `timed_steps`
+    biological seconds (L2 flushed between them), time each kernel, and
+    optionally the end-to-end path through the C ABI from host buffers.
+    Returns the fields of a bench line."""
     import torch
     import torch.distributed as dist
     import synth
-    import __graft_entry__
     from paper_2211_15963_gb300 import dbnet
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if local == 0:
-        __graft_entry__.build()
-    if world > 1:
-        dist.barrier()
-    __graft_entry__.build()
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(dev)  # the library and every event use this stream
-
-    alloc, keep = (None, None) if args.pageable else pinned_alloc(torch)
-    seed = rank_seed(rank)
+    R, S = dims
+    alloc, keep = (None, None) if pageable else pinned_alloc(torch)
     t_gen = time.perf_counter()
-    g = synth.make_graph([args.region_size] * args.regions, args.k_in, seed,
-                         k_within=int(round(0.8 * args.k_in)),
+    g = synth.make_graph([S] * R, args.k_in, seed, k_within=int(round(0.8 * args.k_in)),
                          d_within=(1, 50), d_cross=(50, 200), alloc=alloc)
     if args.two_weights:
         g = synth.with_second_weight(g, seed + 5, alloc=alloc)
     t_gen = time.perf_counter() - t_gen
     params = params_for(args.rate, args.k_in)
-    opts = dict(seed=seed + 1, net_id=rank)
+    opts = dict(seed=seed + 1, net_id=rank, bin_spikes=1 if args.bin_spikes else 0)
 
+    t_create = time.perf_counter()
     net = dbnet.Network(g, params, opts, stream)
-    for _ in range(args.warmup):
+    net.sync()
+    t_create = time.perf_counter() - t_create
+    for _ in range(warmup):
         net.step(STEPS_PER_BIO_S)
     net.sync()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(timed_steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(timed_steps)]
     s0 = net.stats()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0) if clocked else None
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    if clocks:
+        clocks.start()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(timed_steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         starts[k].record(stream)
@@ -305,46 +349,59 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - wall0
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     s1 = net.stats()
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     events = s1["events"] - s0["events"]
     spikes = s1["spikes"] - s0["spikes"]
     events_all, spikes_all, neurons_all, ms_all = combine_ranks(
         events, spikes, g.n_neurons, dev_ms, world, dev)
-    ms_per_step = ms_all / args.steps
-    value = events_all / (ms_all * 1e-3)
+    ms_per_step = ms_all / timed_steps
 
     # per-kernel device time (each kernel between CUDA events on the stream)
     p0 = net.stats()
-    t_del, t_upd = net.step_timed(args.profile_steps)
+    t_del, t_upd = net.step_timed(profile_steps)
     p1 = net.stats()
-    n_prof = args.profile_steps
-    ev_per_launch = (p1["events"] - p0["events"]) / n_prof
+    ev_per_launch = (p1["events"] - p0["events"]) / profile_steps
     hbm, peak_kind = peaks()
     two = args.two_weights
     upd_bytes = g.n_neurons * (UPDATE_BYTES_PER_NEURON_FOUR if two else UPDATE_BYTES_PER_NEURON)
     del_bytes = ev_per_launch * (DELIVER_BYTES_PER_EVENT_TWO if two else DELIVER_BYTES_PER_EVENT)
-    summary = "traffic_mid_network_two_weights.md" if two else "traffic_mid_network.md"
+    tag = "%s_%dhz%s" % ("large_network" if g.n_neurons >= 20_000_000 else "mid_network",
+                         args.rate, "_two_weights" if two else "")
     kern = {
-        "k_update": {"avg_us": 1e3 * t_upd / n_prof, "algorithmic_bytes": upd_bytes,
-                     "achieved_gbs": upd_bytes / (t_upd / n_prof * 1e-3) / 1e9,
-                     "traffic": measured_traffic("k_update", summary)},
-        "k_deliver": {"avg_us": 1e3 * t_del / n_prof, "algorithmic_bytes": del_bytes,
+        "k_update": {"avg_us": 1e3 * t_upd / profile_steps, "algorithmic_bytes": upd_bytes,
+                     "achieved_gbs": upd_bytes / (t_upd / profile_steps * 1e-3) / 1e9,
+                     "traffic": measured_traffic("k_update", "traffic_%s.md" % tag)},
+        "k_deliver": {"avg_us": 1e3 * t_del / profile_steps, "algorithmic_bytes": del_bytes,
                       "events_per_launch": ev_per_launch,
-                      "achieved_gbs": del_bytes / (t_del / n_prof * 1e-3) / 1e9,
-                      "traffic": measured_traffic("k_deliver", summary)},
+                      "achieved_gbs": del_bytes / (t_del / profile_steps * 1e-3) / 1e9,
+                      "traffic": measured_traffic("k_deliver", "traffic_%s.md" % tag)},
     }
+    for k in kern.values():
+        k["frac"] = k["achieved_gbs"] / hbm
     dom = "k_update" if t_upd >= t_del else "k_deliver"
+    step_bytes = upd_bytes + del_bytes
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / hbm, "traffic": kern[dom]["traffic"],
+            "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": kern[dom]["traffic"],
             "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "kernels": kern}
+            "kernels": kern,
+            "kernel_timing": "CUDA events around every launch on the library's stream over %d "
+                             "direct (not graph-replayed) steps" % profile_steps,
+            "path": {"what": "update + delivery algorithmic bytes per Euler step / the timed "
+                             "graph-replayed step time (%d + %d B per neuron and event)"
+                             % (UPDATE_BYTES_PER_NEURON_FOUR if two else UPDATE_BYTES_PER_NEURON,
+                                DELIVER_BYTES_PER_EVENT_TWO if two else DELIVER_BYTES_PER_EVENT),
+                     "achieved": step_bytes / (ms_per_step / STEPS_PER_BIO_S * 1e-3) / 1e9,
+                     "frac": step_bytes / (ms_per_step / STEPS_PER_BIO_S * 1e-3) / 1e9 / hbm}}
+    stats = net.stats()
     net.close()
+    del flush
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from host buffers: create from the host
+    # graph, one biological second, stats and BOLD read, destroy
     e2e = None
-    if args.e2e_steps > 0:
+    if e2e_steps > 0:
         h2d = (g.row_ptr.nbytes + 4 * g.n_edges + (4 if two else 2) * g.n_edges + g.n_edges +
                g.region_offsets.nbytes + g.n_exc.nbytes + 200 * g.n_regions)
         d2h = 8 * g.n_regions + 96
@@ -353,7 +410,7 @@ def run_ours(args):
             dist.barrier()
         t0 = time.perf_counter()
         ev_e2e = 0
-        for _ in range(args.e2e_steps):
+        for _ in range(e2e_steps):
             h = dbnet.dbnet_create(g, params, opts, stream)
             dbnet.dbnet_step(h, STEPS_PER_BIO_S)
             st = dbnet.dbnet_stats(h)
@@ -368,31 +425,120 @@ def run_ours(args):
             dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
         e2e = {"value": float(ev_t.item()) / float(t_e2e.item()), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "what": "dbnet_create from " + ("pageable" if args.pageable else "pinned") +
+               "what": "dbnet_create from " + ("pageable" if pageable else "pinned") +
                        " host graph + 1 biological second + stats and "
                        "BOLD read + destroy, per step (includes the onset transient)",
-               "steps": args.e2e_steps, "bold_samples": int(len(y))}
+               "steps": e2e_steps, "bold_samples": int(len(y))}
+    out = {
+        "value": events_all / (ms_all * 1e-3), "ms_per_step": ms_per_step,
+        "rtf": ms_per_step / 1e3,
+        "neuron_updates_per_s": neurons_all * STEPS_PER_BIO_S * timed_steps / (ms_all * 1e-3),
+        "mean_rate_hz": spikes_all / neurons_all / timed_steps,
+        "wall_s_timed": wall, "generate_s": t_gen, "create_s": t_create,
+        "deliver_blocks": stats["deliver_blocks"], "segment_ring_spikes": stats["seg_ring"],
+        "clocks": clk, "e2e": e2e, "gpu_launches": LAUNCHES_PER_BIO_S * timed_steps,
+        "roofline": roof,
+    }
+    del g, keep
+    return out
 
+
+# -------------------------------------------------------------- our arm ----
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)  # the library and every event use this stream
+    dims = workload_dims(args)
+    large = dims[0] * dims[1] >= 20_000_000
+
+    # the compact lines and the CPU sample come first: the large graph takes
+    # most of the host memory once it is generated
+    extras = {}
+    if args.workload == "large" and not args.no_extras and world == 1:
+        extras = run_extras(args, stream, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(params)
+        cpu = oracle_sample(args, dims)
 
+    res = run_network(args, dims, stream, dev, world, rank, rank_seed(rank, large), args.steps,
+                      args.warmup, args.e2e_steps, args.profile_steps,
+                      pageable=args.pageable or large)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators, f64 BOLD",
-            "data": "synthetic (seeded generator)", "config": workload_config(args, world),
-            "rtf": ms_per_step / 1e3,
-            "neuron_updates_per_s": neurons_all * STEPS_PER_BIO_S * args.steps / (ms_all * 1e-3),
-            "mean_rate_hz": spikes_all / neurons_all / args.steps,
-            "wall_s_timed": wall, "generate_s": t_gen,
-            "clocks": clk, "e2e": e2e, "gpu_launches": 2 * STEPS_PER_BIO_S * args.steps,
-            "roofline": roof, "cpu_baseline": cpu,
+            "metric": METRIC, "value": res.pop("value"), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 state, bf16 weights, int32 fixed-point accumulators, f64 BOLD",
+            "data": "synthetic (seeded generator)", "config": workload_config(args, world, dims),
         }
+        line.update(res)
+        line["cpu_baseline"] = cpu
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_extras(args, stream, dev):
+    """Compact lines of the other workloads, measured in the same run: the
+    mid-size network, the 10,000-neuron network, the batched HMDA ensemble
+    and the request server, each against its own comparison."""
+    out = {}
+    mid_args = argparse.Namespace(**dict(vars(args), workload="mid", regions=None,
+                                         region_size=None))
+    m = run_network(mid_args, WORKLOAD_DIMS["mid"], stream, dev, 1, 0, rank_seed(0, False), 3, 1,
+                    0, 1000, pageable=False)
+    kern = m["roofline"]["kernels"]
+    out["mid"] = {"config": workload_config(mid_args, 1, WORKLOAD_DIMS["mid"])["workload"],
+                  "value": m["value"], "unit": UNIT, "rtf": m["rtf"], "steps": 3, "warmup": 1,
+                  "mean_rate_hz": m["mean_rate_hz"], "deliver_blocks": m["deliver_blocks"],
+                  "k_update_us": kern["k_update"]["avg_us"], "k_update_frac": kern["k_update"]["frac"],
+                  "k_deliver_us": kern["k_deliver"]["avg_us"],
+                  "k_deliver_frac": kern["k_deliver"]["frac"],
+                  "path_frac": m["roofline"]["path"]["frac"], "clocks": m["clocks"]}
+    small_args = argparse.Namespace(**dict(vars(args), steps=3, warmup=2, profile_steps=2000))
+    s = run_small(small_args, stream)
+    out["small"] = {k: s[k] for k in ("config", "value", "unit", "rtf", "events_per_s",
+                                      "mean_rate_hz", "kernels_us", "clocks")}
+    out["small"]["config"] = s["config"]["workload"]
+    ens_args = argparse.Namespace(**dict(vars(args), steps=3, warmup=1, members=64, separate_trs=1))
+    e = run_ensemble(ens_args, stream)
+    out["batched"] = {"config": e["config"]["workload"], "value": e["value"], "unit": UNIT,
+                      "trs": 3, "rtf_ensemble": e["rtf_ensemble"],
+                      "analysis_ms_per_tr": e["analysis_ms_per_tr"],
+                      "separate_value": e["separate"]["value"],
+                      "batched_over_separate": e["batched_over_separate"],
+                      "bold_fit": e["bold_fit"], "clocks": e["clocks"]}
+    srv_args = argparse.Namespace(**dict(vars(args), requests=50, separate_requests=20))
+    v = run_serving(srv_args, stream)
+    out["served"] = {"config": v["config"]["workload"], "value": v["value"], "unit": UNIT,
+                     "latency_per_bio_s": v["latency_per_bio_s"], "failed": v["failed"],
+                     "saturated_value": v["saturated"]["value"],
+                     "separate_value": v["separate"]["value"],
+                     "separate_latency_per_bio_s": v["separate"]["latency_per_bio_s"],
+                     "served_over_separate": v["served_over_separate"], "clocks": v["clocks"]}
+    torch_empty_cache()
+    return out
+
+
+def torch_empty_cache():
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
 
 # ------------------------------------------------------ ensemble workload ----
@@ -431,7 +577,7 @@ def member_params(base, th):
     return out
 
 
-def run_ensemble(args):
+def run_ensemble(args, stream=None):
     import numpy as np
     import torch
     import synth
@@ -441,7 +587,7 @@ def run_ensemble(args):
     __graft_entry__.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(dev)
+    stream = stream or torch.cuda.Stream(dev)
     M = args.members
     g, base, theta, hidden_th = ensemble_setup(M)
     R = g.n_regions
@@ -547,7 +693,7 @@ def run_ensemble(args):
         "batched_over_separate": value / sep_value,
         "clocks": clk, "gpu_launches": args.steps * (2 * TR_STEPS + 14),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------- serving workload ----
@@ -599,7 +745,7 @@ def serving_trace(args):
     return cat, reqs
 
 
-def run_serving(args):
+def run_serving(args, stream=None):
     import numpy as np
     import torch
     import __graft_entry__
@@ -607,7 +753,7 @@ def run_serving(args):
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    stream = stream or torch.cuda.Stream(torch.device("cuda", 0))
     t_gen = time.perf_counter()
     cat, reqs = serving_trace(args)
     t_gen = time.perf_counter() - t_gen
@@ -712,7 +858,7 @@ def run_serving(args):
         "served_over_separate": (sat_events / sat_wall) / (sep_events / sum(service)),
         "clocks": clk, "gpu_launches": launches,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ----------------------------------------------- NEST-comparison workload ----
@@ -730,7 +876,7 @@ NEST_DRIVE = {4.1: 0.55, 12.1: 0.9}
 NEST_PAPER_RTF = {4.1: (4.49, 6.02, 7.49, 9.18, 17.79), 12.1: (7.99, 6.28, 7.82, 17.05, 24.32)}
 
 
-def run_nest(args):
+def run_nest(args, stream=None):
     import torch
     import synth
     import __graft_entry__
@@ -738,7 +884,7 @@ def run_nest(args):
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    stream = stream or torch.cuda.Stream(torch.device("cuda", 0))
     table = []
     clocks = ClockSampler(0)
     clocks.start()
@@ -785,11 +931,11 @@ def run_nest(args):
         "paper_context": "Supplementary Table 4: one GPU with 16 GB HBM2 (10.8 TFLOPS), "
                          "their own connectome-derived networks",
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------ small network ----
-def run_small(args):
+def run_small(args, stream=None):
     """The 10,000-neuron network (one region, in-degree 100, delays 1-20
     steps, 10 Hz Poisson drive per neuron).  Its working set (~2 MB of state,
     6 MB of edges) stays in the L2, so the step is bound by launch and
@@ -802,7 +948,7 @@ def run_small(args):
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    stream = stream or torch.cuda.Stream(torch.device("cuda", 0))
     g = synth.small_network()
     p = synth.default_region_params()
     net = dbnet.Network(g, p, dict(seed=synth.seed_for(0) + 1), stream)
@@ -843,7 +989,7 @@ def run_small(args):
                        "k_update": 1e3 * t_upd / args.profile_steps},
         "clocks": clk, "gpu_launches": 2 * n_steps,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------- step-size accuracy study ----
@@ -911,7 +1057,7 @@ def dt_study_table(runs):
     return table
 
 
-def run_dt_study(args):
+def run_dt_study(args, stream=None):
     """Extended Data Fig. 1: membrane potentials of a 1,000-neuron LIF network
     integrated by forward Euler at several steps, against the finest step
     the device's 8-bit refractory counters allow (Tref = 2 ms in 250 steps).
@@ -925,7 +1071,7 @@ def run_dt_study(args):
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    stream = stream or torch.cuda.Stream(torch.device("cuda", 0))
     seed = synth.seed_for(7)
     runs = {}
     for dt in DT_STUDY_MS:
@@ -959,11 +1105,11 @@ def run_dt_study(args):
                          "error at dt 1 ms against 0.001 ms over one second",
         "gpu_launches": int(sum(2 * DT_STUDY_STEPS * round(1.0 / x) for x in DT_STUDY_MS)),
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------- micro-column workload ----
-def run_columns(args):
+def run_columns(args, stream=None):
     """Cortical micro-column network (Extended Data Table 3): 100 voxels of
     20,000 neurons in ten layer populations, mean in-degree 1,000 with a
     heavy-tailed out-degree; the drive is bisected for ~15 Hz on a 5-voxel
@@ -977,7 +1123,7 @@ def run_columns(args):
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    stream = torch.cuda.Stream(torch.device("cuda", 0))
+    stream = stream or torch.cuda.Stream(torch.device("cuda", 0))
     base = synth.scale_for_degree(synth.default_region_params(), 1000)
     sub = synth.cortical_columns(5, 20000, 1000, seed=synth.seed_for(6) + 1)
     drive, rate_sub, _ = tune.tune_drive(sub, base, float(args.rate), knob="I_ext", lo=0.5,
@@ -1024,14 +1170,16 @@ def run_columns(args):
                        "k_update": 1e3 * t_upd / args.profile_steps},
         "generate_s": t_gen, "gpu_launches": 2 * STEPS_PER_BIO_S * args.steps,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # -------------------------------------------------------- reference arm ----
 def run_reference(args):
-    """The CPU oracle, as it stands, on the host cores: each step is a 10 ms
-    (100 Euler steps) sample of the 1/20-scale network after an untimed
-    200 ms onset.  Under torchrun only rank 0 works."""
+    """The CPU oracle, as it stands, on the host cores (its all-core timing
+    variant; results identical to the single-threaded loop): each step is a
+    10 ms (100 Euler steps) sample of a 1/20-scale network of the workload
+    (a twentieth of the regions, same region size, in-degree and drive)
+    after 500 untimed steps.  Under torchrun only rank 0 works."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
@@ -1040,10 +1188,15 @@ def run_reference(args):
     import synth
     oracle.build()
     synth.build()
-    params = params_for(args.rate)
-    g = synth.mid_network(n_regions=5, seed=synth.seed_for(1) + 100)
-    s = oracle.Sim(g, params, seed=synth.seed_for(1) + 1, precision=32)
-    s.step(2000)
+    R, S = workload_dims(args)
+    r_s = max(1, R // 20)
+    g = synth.make_graph([S] * r_s, args.k_in, synth.seed_for(1) + 100,
+                         k_within=int(round(0.8 * args.k_in)) if r_s > 1 else args.k_in,
+                         d_within=(1, 50), d_cross=(50, 200))
+    threads = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
+    s = oracle.Sim(g, params_for(args.rate, args.k_in), seed=synth.seed_for(1) + 1, precision=32,
+                   threads=threads, bin_spikes=args.bin_spikes)
+    s.step(500)
     for _ in range(args.warmup):
         s.step(100)
     i0 = s.info()
@@ -1054,15 +1207,24 @@ def run_reference(args):
     i1 = s.info()
     ev = i1["events"] - i0["events"]
     value = ev / wall
-    sample = ("%d x 100 Euler steps (10 ms biological each) of a 100,000-neuron, "
-              "in-degree-1,000 1/20-scale network after a 200 ms untimed onset" % args.steps)
+    cfg = workload_config(args, world, (r_s, S))
+    cfg["workload"] = ("1/20-scale CPU sample of the %s (%s neurons): %s neurons, %d regions x %s, "
+                       "in-degree %s, dt 0.1 ms, ~%d Hz"
+                       % (network_name(R * S), f"{R * S:,}", f"{r_s * S:,}", r_s, f"{S:,}",
+                          f"{args.k_in:,}", args.rate))
+    cfg["step"] = "100 Euler steps (10 ms biological)"
+    sample = ("%d x 100 Euler steps (10 ms biological each) of a %s-neuron 1/20-scale network "
+              "(%d regions x %s, in-degree %s) after 500 untimed steps; the matched-FP32 oracle's "
+              "all-core timing variant on %d threads (%s)"
+              % (args.steps, f"{g.n_neurons:,}", r_s, f"{S:,}", f"{args.k_in:,}", threads,
+                 cpu_model()))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (op-order-matched oracle)", "data": "synthetic (seeded generator)",
-        "config": workload_config(args, world),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -1073,18 +1235,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "ensemble":
-        run_ensemble(args)
-    elif args.workload == "serving":
-        run_serving(args)
-    elif args.workload == "nest":
-        run_nest(args)
-    elif args.workload == "columns":
-        run_columns(args)
-    elif args.workload == "dt-study":
-        run_dt_study(args)
-    elif args.workload == "small":
-        run_small(args)
+        return
+    runners = {"ensemble": run_ensemble, "serving": run_serving, "nest": run_nest,
+               "columns": run_columns, "dt-study": run_dt_study, "small": run_small}
+    if args.workload in runners:
+        print(json.dumps(runners[args.workload](args)), flush=True)
     else:
         run_ours(args)
 

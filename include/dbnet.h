@@ -141,12 +141,44 @@ typedef struct {
  *   precision        32 (FP32 state; the only mode the device path runs)
  *   raster_capacity  spikes kept for dbnet_read_spikes (0 = none)
  *   bold_capacity    BOLD samples kept per region
- *   autotune_at      step at which the delivery grid is tuned (-1 = never):
- *                    the next 16 x C steps launch the delivery kernel with
- *                    each of C candidate grids (1..4 blocks per SM) in turn,
- *                    timed by CUDA events, and the fastest is kept.  Results
- *                    do not depend on the grid (integer accumulation).
- *                    Default 2000 (200 ms at dt 0.1 ms, past the onset). */
+ *   autotune_at      step at which the delivery is tuned (-1 = never): with an
+ *                    automatic emit_delay candidate, first D + 64 steps
+ *                    without and D + 64 with it, the last 64 of each timed,
+ *                    the faster kept; then 16 x C steps launch the delivery
+ *                    kernel with each of C candidate grids (1..4 blocks per
+ *                    SM) in turn, timed by CUDA events, and the fastest is
+ *                    kept.  Results do not depend on either choice (integer
+ *                    accumulation).  Default 2000 (200 ms at dt 0.1 ms, past
+ *                    the onset).
+ *   bin_spikes       1: spikes are handed on at bin edges (Supplementary Sec. 3,
+ *                    "Numerical method": the accumulated spike A_j(t) is non-
+ *                    zero only at t = k * bin and marks a spike of j in
+ *                    (t - bin, t]).  A spike emitted in any step of bin
+ *                    [k spb, (k+1) spb) (spb = bin_ms / dt_ms) reaches the
+ *                    targets of its delay-d edges at step (k+1) spb - 1 + d;
+ *                    d = 1 is the paper's scheme.  Needs T_ref >= bin_ms -
+ *                    dt_ms in every region (so a neuron fires at most once
+ *                    per bin and A_j is 0 or 1; else DBNET_EINVAL) and
+ *                    longest delay + spb <= 256.  0 (default): every spike
+ *                    is handed on in its own step.
+ *   emit_delay       which delays are added at emission instead of when they
+ *                    come due (the results are the same: the accumulators
+ *                    are exact integers).  Arrival time reads each due
+ *                    (spike, delay) segment of a row on its own, which pays
+ *                    when segments are long; at emission the accumulators
+ *                    form a ring of D slots (D x N x 8 bytes, taken only when
+ *                    it fits a third of the free device memory) and a
+ *                    spike's edges of delay >= emit_delay go straight into
+ *                    the slot of their arrival step, its short segments read
+ *                    in one pass.  -1 (default): none; d >= 1: delays >= d;
+ *                    0: the delays from which every (row, delay) segment
+ *                    holds fewer than 4 edges on average (estimated from a
+ *                    sample of rows at create), kept only if the autotuner
+ *                    measures it faster than none.  Request servers use none.
+ *                    On the benchmark networks (in-degree 1,000, 1.3 edges
+ *                    per cross-region delay) emission measured slower: its
+ *                    scattered additions land in a ring far larger than the
+ *                    L2. */
 typedef struct {
   double dt_ms, bin_ms, tr_ms, z_scale;
   double bw_kappa, bw_gamma, bw_tau, bw_alpha, bw_rho, bw_V0;
@@ -156,12 +188,15 @@ typedef struct {
   int64_t raster_capacity;
   int64_t bold_capacity;
   int64_t autotune_at;
+  int32_t bin_spikes;
+  int32_t emit_delay;
 } dbnet_options_t;
 
 typedef struct {
   int64_t step;              /* steps completed */
   int64_t spikes;            /* spikes emitted */
-  int64_t events;            /* synaptic events applied to accumulators by the
+  int64_t events;            /* synaptic events: the out-degree of every spike
+                                handed on, counted as it is emitted, by the
                                 engine behind the handle (for an ensemble member:
                                 the whole ensemble) */
   int64_t raster_len;        /* spikes recorded */
@@ -176,11 +211,45 @@ typedef struct {
   int32_t deliver_blocks;    /* delivery grid in use */
   int32_t autotuned;         /* 1 once the autotuner has chosen that grid */
   int32_t two_weights;       /* 1: four accumulator channels (two weights per edge) */
+  int32_t seg_ring;          /* spikes per step whose segments the delivery reads
+                                from its delay-major ring; a step's later spikes
+                                (and graphs with u32 segment tables) are resolved
+                                from the graph's own tables */
+  int32_t emit_delay;        /* delays >= this are added at emission (0: none) */
   int32_t reserved;
 } dbnet_stats_t;
 
 /* Name of a status code (static string). */
 const char* dbnet_strerror(int code);
+
+/* Optional device allocator.  By default every handle takes its device
+ * memory with cudaMalloc and returns it with cudaFree.  A caller that owns a
+ * memory pool -- PyTorch's caching allocator, for instance -- installs an
+ * allocator here, and every device allocation of handles created afterwards
+ * (network state, graph records, rings, ensemble and server buffers, the
+ * server's arena) comes from alloc and goes back to free:
+ *   alloc(bytes, stream, ctx)   returns device memory of at least bytes,
+ *                               aligned to 256 bytes, or NULL (the call that
+ *                               needed it then fails with DBNET_ENOMEM);
+ *                               stream is the cuda_stream given to the create
+ *                               call (NULL: the legacy default stream)
+ *   free(ptr, bytes, stream, ctx) returns it; the handle's stream has been
+ *                               synchronised first, so the memory is idle.
+ * Each allocation goes back to the allocator it came from, so installing
+ * another (or NULL, which restores cudaMalloc) affects only later handles;
+ * the functions and ctx must stay valid until those handles are destroyed.
+ * Process-wide; install it before creating handles, not while another
+ * thread creates one.  The allocation-free entry point never calls it.
+ * (The paper has no counterpart: this serves embedding in a host framework.) */
+typedef void* (*dbnet_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*dbnet_free_fn)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+typedef struct {
+  dbnet_alloc_fn alloc;
+  dbnet_free_fn free;
+  void* ctx;
+} dbnet_allocator_t;
+/* a NULL allocator, or one with NULL functions, restores cudaMalloc */
+int dbnet_set_allocator(const dbnet_allocator_t* allocator);
 
 /* Detail of the last failure on the calling thread (static per thread). */
 const char* dbnet_last_error(void);
@@ -194,14 +263,19 @@ int dbnet_abi_sizes(int64_t* out, int n);
 
 /* Fill *o with the defaults: dt 0.1 ms, bin 1 ms, TR 800 ms, z_scale 1,
  * the standard hemodynamic constants, seed 1, net_id 0, automatic S,
- * precision 32, no raster, 4096 BOLD samples, autotune at step 2000. */
+ * precision 32, no raster, 4096 BOLD samples, autotune at step 2000, no
+ * spike binning, no emission-time delivery. */
 int dbnet_options_default(dbnet_options_t* o);
 
-/* Build a network on the current CUDA device: copy the graph and parameters
- * (edges in chunks of rows through staging buffers), validate them on the
- * device, store the edges as 6-byte (target, BF16 weight) records, choose S
- * and set the initial state (V uniform in [V_reset, V_th) from Philox
- * stream 1; traces zero).  Also builds the per-row delay-segment table
+/* Build a network on the current CUDA device (Methods, "Constructing the
+ * Digital Brain model": the neurons with their property table and the
+ * connection table of Supplementary Table 5, here one network on one GPU):
+ * copy the graph and parameters (edges in chunks of rows through staging
+ * buffers), validate them on the device, store the edges as 6-byte
+ * (target, BF16 weight) records, choose S and set the initial state (V
+ * uniform in [V_reset, V_th) from Philox stream 1, which desynchronises the
+ * neurons as the paper's initial background spikes do, Supplementary Sec. 3;
+ * traces zero).  Also builds the per-row delay-segment table
  * (N x longest delay counts, u16 when every row has < 65536 edges).
  * params: [n_regions].  cuda_stream: a cudaStream_t or NULL.
  * Returns DBNET_EINVAL for a malformed graph or parameter set,
@@ -225,12 +299,18 @@ int dbnet_sync(dbnet_t* h);
 int dbnet_step_timed(dbnet_t* h, int64_t n_steps, double* ms);
 
 /* Recorded spikes with t0 <= step < t1, sorted by (step, id), written to
- * step[] and id[] (capacity cap).  *n_out = number written; DBNET_ERANGE
- * when more than cap match (the first cap are written). */
+ * step[] and id[] (capacity cap): the spike trains the model outputs
+ * (Results, "the output describing the action potentials over time";
+ * Supplementary Algorithm 2's per-step list of spiking neurons).
+ * *n_out = number written; DBNET_ERANGE when more than cap match (the first
+ * cap are written).  A step is the Euler step at whose end V reached V_th. */
 int dbnet_read_spikes(dbnet_t* h, int64_t t0, int64_t t1, int32_t* step, int32_t* id,
                       int64_t cap, int64_t* n_out);
 
-/* BOLD samples y[k][r] (row-major, k-th TR), at most cap_samples rows. */
+/* BOLD samples y[k][r] (row-major, k-th TR), at most cap_samples rows: the
+ * Balloon-Windkessel output of Extended Data Table 4 for each region,
+ * sampled once per TR (800 ms in the paper's fMRI, Supplementary Sec. 1),
+ * the observation HMDA assimilates (Supplementary Sec. 6). */
 int dbnet_read_bold(dbnet_t* h, double* y, int64_t cap_samples, int64_t* n_out);
 
 /* Hemodynamic state x[r][4] = (s, f, v, q) per region. */
@@ -249,6 +329,10 @@ int dbnet_set_state(dbnet_t* h, const float* V, const float* J, const int32_t* r
 int dbnet_read_ibg(dbnet_t* h, float* I_bg);
 int dbnet_set_ibg(dbnet_t* h, const float* I_bg);
 
+/* Counters of the run: steps, spikes, synaptic events (every out-edge of
+ * every spike handed on, as Supplementary Algorithm 2 pushes them; the
+ * paper's throughput figures count the same events), raster and BOLD
+ * lengths, and the shapes the engine chose. */
 int dbnet_stats(dbnet_t* h, dbnet_stats_t* out);
 
 void dbnet_destroy(dbnet_t* h);

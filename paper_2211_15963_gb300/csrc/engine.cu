@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,17 @@ namespace dbn {
 
 thread_local std::string g_last_error;
 thread_local Arena* g_arena = nullptr;
+thread_local void* g_alloc_stream = nullptr;
+
+namespace {
+std::mutex g_hook_mu;
+AllocHook g_hook;
+}  // namespace
+
+AllocHook current_alloc_hook() {
+  std::lock_guard<std::mutex> lock(g_hook_mu);
+  return g_hook;
+}
 
 // ---------------------------------------------------------------- graph ----
 std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
@@ -67,6 +79,21 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   int64_t max_out = 0;
   for (int32_t j = 0; j < N; ++j) max_out = std::max(max_out, g->row_ptr[j + 1] - g->row_ptr[j]);
   gd->seg_kind = max_out < 65536 ? kSeg16 : kSeg32;  // u16 counts when every row is short
+  // edges per row and delay on a sample of rows: the delays from which all
+  // segments are short enough to hand on at emission
+  {
+    const int32_t every = std::max<int32_t>(1, N / 65536);
+    std::vector<double> per_delay(256, 0.0);
+    int64_t rows = 0;
+    for (int32_t j = 0; j < N; j += every, ++rows)
+      for (int64_t e = g->row_ptr[j]; e < g->row_ptr[j + 1]; ++e) per_delay[g->delay[e]] += 1.0;
+    int32_t from = 0;
+    for (int32_t d = gd->max_delay; d >= 1 && rows > 0; --d) {
+      if (per_delay[(size_t)d] / (double)rows >= kEmitSegEdges) break;
+      from = d;
+    }
+    gd->emit_from = E > 0 ? from : 0;
+  }
   const int32_t per16 = gd->seg_kind == kSeg16 ? 8 : 4;  // entries per 16 bytes
   gd->seg_stride = (gd->max_delay + per16 - 1) / per16 * per16;
   const int64_t seg_bytes = (int64_t)N * gd->seg_stride * (gd->seg_kind == kSeg16 ? 2 : 4);
@@ -74,7 +101,7 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   gd->row_ptr.alloc(N + 1);
   gd->ro.alloc(R + 1);
   gd->two_w = g->weight2 != nullptr;
-  gd->rec.alloc(std::max<int64_t>((gd->two_w ? 4 : 3) * E, 4));
+  gd->rec.alloc((gd->two_w ? 4 : 3) * E + 4);  // 8 bytes of padding: the delivery reads whole words
   gd->seg.alloc(seg_bytes);
   CK(cudaMemcpyAsync(gd->row_ptr.p, g->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(gd->ro.p, g->region_offsets, sizeof(int32_t) * (R + 1), cudaMemcpyHostToDevice, s));
@@ -141,8 +168,14 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
 // ---------------------------------------------------- region constants ----
 static bool finite(double x) { return std::isfinite(x); }
 
-void check_params(const dbnet_region_params_t& p, double dt) {
+int32_t bin_lead(const dbnet_options_t& o) {
+  return o.bin_spikes ? (int32_t)std::lrint(o.bin_ms / o.dt_ms) - 1 : 0;
+}
+
+void check_params(const dbnet_region_params_t& p, double dt, int32_t min_ref) {
   if (!(p.C > 0) || !finite(p.C)) raise(DBNET_EINVAL, "C must be > 0");
+  if (std::lrint(p.Tref / dt) < min_ref)
+    raise(DBNET_EINVAL, "with spike binning T_ref must be at least one bin minus one step");
   if (!(p.gL >= 0) || !finite(p.gL)) raise(DBNET_EINVAL, "gL must be >= 0");
   for (double v : {p.VL, p.Vth, p.Vreset, p.I_ext})
     if (!finite(v)) raise(DBNET_EINVAL, "non-finite membrane constant");
@@ -275,6 +308,8 @@ void check_options(const dbnet_options_t& o) {
   if (!finite(o.z_scale)) raise(DBNET_EINVAL, "z_scale must be finite");
   if (o.fixed_shift < 0 || o.fixed_shift > 30) raise(DBNET_EINVAL, "fixed_shift must be in 0..30");
   if (o.autotune_at < -1) raise(DBNET_EINVAL, "autotune_at must be -1 or a step index");
+  if (o.bin_spikes != 0 && o.bin_spikes != 1) raise(DBNET_EINVAL, "bin_spikes must be 0 or 1");
+  if (o.emit_delay < -1 || o.emit_delay > 255) raise(DBNET_EINVAL, "emit_delay must be -1..255");
 }
 
 // --------------------------------------------------------------- engine ----
@@ -300,7 +335,20 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
     for (const auto& p : sp.params) any_ext = any_ext || ext_bits(p) != 0;
     four = four || sp.graph->two_w;
   }
-  init_pool(n, tiles, regions, dmax_all + 1, specs[0].opt, user_stream, any_ext, four);
+  // delays handed on at emission: the option, or (0) the graphs' own
+  // threshold (instances share one graph in an ensemble)
+  int32_t emit_from = 0;
+  const int32_t want = specs[0].opt.emit_delay;
+  if (want > 0) {
+    emit_from = want;
+  } else if (want == 0) {
+    emit_from = specs[0].graph->emit_from;
+    for (const auto& sp : specs)
+      if (sp.graph->emit_from != emit_from) emit_from = 0;
+  }
+  // with spike binning a spike waits up to spb - 1 steps for its bin to end
+  init_pool(n, tiles, regions, dmax_all + 1 + bin_lead(specs[0].opt), specs[0].opt, user_stream,
+            any_ext, four, emit_from > dmax_all ? 0 : emit_from);
   int64_t t = 0;
   int32_t r = 0;
   for (int k = 0; k < n; ++k) {
@@ -314,7 +362,7 @@ void Engine::init(const std::vector<InstSpec>& specs, void* user_stream) {
 
 void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
                        const dbnet_options_t& common, void* user_stream, bool any_ext,
-                       bool four) {
+                       bool four, int32_t emit_from) {
   if (user_stream) {
     stream = (cudaStream_t)user_stream;
     own_stream = false;
@@ -337,13 +385,28 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   Ibg.alloc(stride);
   fext.alloc(stride);
   ref.alloc(stride);
-  acc.alloc((four ? 2 : 1) * stride);  // int2 per neuron, or int4 with four channels
+  // accumulators: one slot, or a ring of D slots when long delays may be
+  // handed on at emission (and the ring takes at most a third of the free
+  // memory)
+  int32_t slots = 1;
+  if (emit_from > 0) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double ring_b = (double)D * (double)stride * 8.0 * (four ? 2.0 : 1.0);
+    if (ring_b <= (double)free_b / 3.0) slots = D;
+    else emit_from = 0;
+  }
+  acc.alloc((four ? 2 : 1) * stride * (int64_t)slots);  // int2 per neuron, or int4 with four channels
   CK(cudaMemsetAsync(Ibg.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(fext.p, 0, sizeof(float) * stride, stream));  // read only where kExtHet
   CK(cudaMemsetAsync(V.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(J.p, 0, sizeof(float) * 4 * stride, stream));
   CK(cudaMemsetAsync(ref.p, 0, stride, stream));
-  CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * (four ? 2 : 1) * stride, stream));
+  CK(cudaMemsetAsync(acc.p, 0, sizeof(int2) * (four ? 2 : 1) * stride * (size_t)slots, stream));
+  if (slots > 1) {
+    slot_emit.alloc(D);
+    CK(cudaMemsetAsync(slot_emit.p, 0xFF, sizeof(uint16_t) * D, stream));  // none yet
+  }
   desc.alloc(n_inst);
   dyn.alloc(n_inst);
   tile_info.alloc(tiles);
@@ -404,6 +467,20 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev.ref = ref.p;
   dev.acc = acc.p;
   dev.stride = stride;
+  dev.acc_slots = slots;
+  // V, J, ref, the step's accumulators (and the OU current) held in the L2
+  // across steps when together they take at most half of it
+  {
+    int dev_id = 0, l2 = 0;
+    CK(cudaGetDevice(&dev_id));
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev_id));
+    const double state_b = (double)stride * (4.0 + 16.0 + 1.0 + (four ? 16.0 : 8.0) + (any_ext ? 8.0 : 0.0));
+    dev.state_resident = state_b <= 0.5 * (double)l2 ? 1 : 0;
+  }
+  dev.d_emit = emit_from > 0 ? emit_from : D + 1;
+  dev.slot_emit = slots > 1 ? slot_emit.p : nullptr;
+  emit_cand = emit_from;
+  emit_phase = (emit_from > 0 && common.emit_delay == 0 && common.autotune_at >= 0) ? 0 : 2;
   dev.insts = desc.p;
   dev.dyn = dyn.p;
   dev.tile_info = tile_info.p;
@@ -419,6 +496,8 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev.hr0 = hr0.p;
   dev.seg_cap = seg_cap;
   dev.dcap = dcap;
+  dev.bin_lead = bin_lead(common);
+  if (dev.bin_lead >= D - 1) raise(DBNET_EINVAL, "the spike bin is longer than the ring");
   dev.D = D;
   dev.events = events.p;
   dev.flags = flags.p;
@@ -433,10 +512,10 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
     CK(cudaGetDevice(&dev_id));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
     for (int k = 1; k <= 4 && sms * k <= del_grid; ++k) tune_grid.push_back(sms * k);
+    tune_at = (unsigned long long)common.autotune_at;
     if (tune_grid.size() > 1) {
       tune_ms.assign(tune_grid.size(), 0.0);
       tune_pending = true;
-      tune_at = (unsigned long long)common.autotune_at;
     }
   }
   CK(cudaGetLastError());
@@ -449,7 +528,8 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
   if (k < 0 || k >= cap_inst || first_tile < 0 || first_tile + nt > cap_tiles || rbase < 0 ||
       rbase + g.R > cap_R)
     raise(DBNET_EINVAL, "instance placement outside the engine's capacity");
-  if (g.max_delay >= dev.D) raise(DBNET_EINVAL, "a delay is longer than the engine's ring");
+  if (g.max_delay + dev.bin_lead >= dev.D) raise(DBNET_EINVAL, "a delay is longer than the engine's ring");
+  if (bin_lead(sp.opt) != dev.bin_lead) raise(DBNET_EINVAL, "spike binning differs from the engine's");
   if (g.two_w && !dev.four)
     raise(DBNET_EUNSUPPORTED, "two weights per edge need an engine with four accumulator channels");
   InstHost& ih = inst[(size_t)k];
@@ -476,6 +556,7 @@ void Engine::place(int k, const InstSpec& sp, int32_t first_tile, int32_t rbase,
   d.row_ptr = g.row_ptr.p;
   d.rec = g.rec.p;
   d.two_w = g.two_w ? 1 : 0;
+  d.bin_sp = sp.opt.bin_spikes ? 1 : 0;
   d.col = nullptr;
   d.w = nullptr;
   d.delay = nullptr;
@@ -586,6 +667,8 @@ void Engine::set_extent(int32_t tiles, int32_t regions) {
 
 Engine::~Engine() {
   if (gexec) cudaGraphExecDestroy(gexec);
+  for (auto& ev : emit_ev)
+    if (ev) cudaEventDestroy(ev);
   if (own_stream && stream) {
     cudaStreamSynchronize(stream);
     cudaStreamDestroy(stream);
@@ -624,16 +707,63 @@ void Engine::step(int64_t n) {
   if (n < 0) raise(DBNET_EINVAL, "n_steps must be >= 0");
   if (n == 0) return;
   while (n > 0) {
-    if (tune_pending && g_host >= tune_at) {
+    const bool emit_pending = emit_phase < 2;
+    if (emit_pending && g_host >= tune_at) {  // the emission threshold first,
+      n -= tune_emit(n);
+      continue;
+    }
+    if (tune_pending && g_host >= tune_at) {  // then the grid
       n -= tune_steps(n);
       continue;
     }
-    const int64_t k = tune_pending ? std::min<int64_t>(n, (int64_t)(tune_at - g_host)) : n;
+    const int64_t k = (tune_pending || emit_pending) ? std::min<int64_t>(n, (int64_t)(tune_at - g_host)) : n;
     run_plain(k);
     n -= k;
   }
   launch_close(dev, g_host, stream);
   CK(cudaGetLastError());
+}
+
+void Engine::set_emit(int32_t d) {
+  if (d == dev.d_emit) return;
+  dev.d_emit = d;
+  if (gexec) {  // the captured steps carry the old threshold
+    CK(cudaStreamSynchronize(stream));
+    CK(cudaGraphExecDestroy(gexec));
+    gexec = nullptr;
+  }
+}
+
+// Up to n steps of the emission tuner: phase 0 runs without emission, phase
+// 1 with the candidate threshold; each runs D steps for the spikes already
+// in flight to come due under its rule, then kEmitTimed whole steps between
+// two events.  The faster rule stays.  Returns the steps run.
+int64_t Engine::tune_emit(int64_t n) {
+  const int64_t warm = dev.D, per = warm + kEmitTimed;
+  if (emit_steps == 0) set_emit(emit_phase == 0 ? dev.D + 1 : emit_cand);
+  if (!emit_ev[0]) {
+    CK(cudaEventCreate(&emit_ev[0]));
+    CK(cudaEventCreate(&emit_ev[1]));
+  }
+  const int64_t k = std::min<int64_t>(n, per - emit_steps);
+  int64_t ran = 0;
+  while (ran < k) {
+    if (emit_steps == warm) CK(cudaEventRecord(emit_ev[0], stream));
+    const int64_t chunk = emit_steps < warm ? std::min<int64_t>(k - ran, warm - emit_steps) : k - ran;
+    run_plain(chunk);
+    ran += chunk;
+    emit_steps += chunk;
+  }
+  if (emit_steps == per) {
+    CK(cudaEventRecord(emit_ev[1], stream));
+    CK(cudaEventSynchronize(emit_ev[1]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, emit_ev[0], emit_ev[1]));
+    emit_ms[emit_phase] = ms;
+    emit_steps = 0;
+    if (++emit_phase == 2) set_emit(emit_ms[1] < emit_ms[0] ? emit_cand : dev.D + 1);
+  }
+  return k;
 }
 
 // Up to n steps of the autotuner: step i of the tuning run launches its
@@ -821,6 +951,16 @@ int dbnet_abi_sizes(int64_t* out, int n) {
   return 10;
 }
 
+int dbnet_set_allocator(const dbnet_allocator_t* a) {
+  std::lock_guard<std::mutex> lock(g_hook_mu);
+  if (a && ((a->alloc == nullptr) != (a->free == nullptr))) {
+    g_last_error = "an allocator needs both alloc and free";
+    return DBNET_EINVAL;
+  }
+  g_hook = (a && a->alloc) ? AllocHook{a->alloc, a->free, a->ctx} : AllocHook{};
+  return DBNET_OK;
+}
+
 int dbnet_options_default(dbnet_options_t* o) {
   if (!o) return DBNET_EINVAL;
   std::memset(o, 0, sizeof(*o));
@@ -841,6 +981,7 @@ int dbnet_options_default(dbnet_options_t* o) {
   o->raster_capacity = 0;
   o->bold_capacity = 4096;
   o->autotune_at = 2000;
+  o->emit_delay = -1;
   return DBNET_OK;
 }
 
@@ -850,11 +991,13 @@ int dbnet_create(const dbnet_graph_t* graph, const dbnet_region_params_t* params
   std::unique_ptr<dbnet> h(new (std::nothrow) dbnet());
   if (!h) return DBNET_ENOMEM;
   int rc = guarded(nullptr, [&] {
+    AllocStreamScope alloc_stream(cuda_stream);
     if (!out || !params || !options) raise(DBNET_EINVAL, "NULL argument");
     check_options(*options);
     if (!graph) raise(DBNET_EINVAL, "graph is NULL");
     if (graph->n_regions < 1) raise(DBNET_EINVAL, "n_regions must be >= 1");
-    for (int32_t r = 0; r < graph->n_regions; ++r) check_params(params[r], options->dt_ms);
+    for (int32_t r = 0; r < graph->n_regions; ++r)
+      check_params(params[r], options->dt_ms, bin_lead(*options));
     cudaStream_t s = (cudaStream_t)cuda_stream;
     auto g = upload_graph(graph, s);
     InstSpec sp;
@@ -1036,6 +1179,8 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     out->packed_edges = ih.graph->packed ? 1 : 0;
     out->weights_rounded = ih.graph->rounded ? 1 : 0;
     out->deliver_blocks = e.del_grid;
+    out->seg_ring = ih.graph->seg_kind == kSeg16 ? (int32_t)e.dev.seg_cap : 0;
+    out->emit_delay = e.dev.d_emit <= e.dev.D ? e.dev.d_emit : 0;
     out->autotuned = (!e.tune_pending && !e.tune_grid.empty()) ? 1 : 0;
     out->two_weights = e.dev.four;
   });

@@ -25,10 +25,19 @@
 // Iteration g of an engine runs k_deliver then k_update; the bin that ends
 // with iteration g - 1 is closed (Balloon-Windkessel step, BOLD sample) at
 // the start of k_deliver(g), one region per thread.
-// Spike ring: D slots; slot n mod D lists the spikes of step n as
+// Spike ring: D slots; slot n mod D lists the spikes handed on at step n
+//   (their own step, or the last step of their bin with spike binning) as
 //   global index | class << 31, with a count per slot.  At step n the
 //   delivery reads slots n - d (d = 1..D-1) and applies, for each listed
-//   spike, the segment of its row whose delay is exactly d.
+//   spike, the segment of its row whose delay is exactly d (arrival time).
+// Long delays at emission: when d_emit <= the longest delay, the
+//   accumulators form a ring of D slots (slot a mod D collects the arrivals
+//   of step a); at step n the delivery adds, for every spike handed on at
+//   step n - 1, its edges of delay d >= d_emit straight into slot n - 1 + d,
+//   each (spike, delay) segment read as it lies in the row, so that the
+//   short segments of long delays cost one coalesced pass instead of one
+//   resolution each; arrival time keeps the delays below d_emit.  The
+//   update of step n reads and clears slot n.
 // Delay-major segment ring (u16 tables only): k_deliver(n) copies, for the
 //   first seg_cap spikes of step n - 1, the row start into hr0[slot][k] and
 //   the row's segment counts into hseg[slot][d][k] (d < dcap), so that the
@@ -128,7 +137,8 @@ struct alignas(16) InstDesc {
   float two_S, inv_two_S;
   int32_t spb, bins_per_tr;
   int32_t seg_kind, dmax, seg_stride, ext;  // ext: kExt* bits of any region
-  int32_t two_w, pad_w;          // two_w: 8-byte records with a second weight
+  int32_t two_w, bin_sp;         // two_w: 8-byte records with a second weight; bin_sp:
+                                 //   spikes handed on at the end of their bin
   double h_bw, z_scale, kappa, gamma, tau, alpha, rho, V0;
 };
 
@@ -159,8 +169,13 @@ struct EngineDev {
   float* Ibg;            // background OU current per neuron
   float* fext;           // per-neuron injected-current factor (1 where homogeneous)
   uint8_t* ref;
-  int2* acc;
+  int2* acc;             // [acc_slots][stride] (int2, or int4 with four channels)
   int64_t stride;
+  int32_t acc_slots;     // 1, or D when long delays are handed on at emission
+  int32_t d_emit;        // delays >= d_emit are added at emission into the slot
+                         //   of their arrival step (D + 1: none)
+  uint16_t* slot_emit;   // [D] d_emit in force when each ring slot's spikes were
+                         //   handed on (their delays below it arrive later)
   const InstDesc* insts;
   InstDyn* dyn;
   const int4* tile_info;  // per tile: instance, first region (local), regions touched, 0
@@ -175,12 +190,14 @@ struct EngineDev {
   uint16_t* hseg;        // [D][dcap][seg_cap]
   int64_t* hr0;          // [D][seg_cap]
   int64_t seg_cap;       // 0: no segment ring
-  int32_t dcap, pad_h;
+  int32_t dcap;
+  int32_t bin_lead;      // spike binning: steps per bin - 1 (else 0)
   unsigned long long* events;
   unsigned int* flags;
   int32_t D;
   int32_t n_inst, n_tiles, total_R;
   int32_t any_ext;       // launch the update variant with the kExt* terms
+  int32_t state_resident;  // the neuron state fits the L2: keep it there between steps
   int32_t four;          // four accumulator channels per neuron (acc as int4)
 };
 

@@ -337,6 +337,7 @@ int ens_create(const dbnet_graph_t* graph, const dbnet_region_params_t* base, in
   std::unique_ptr<dbens> h(new (std::nothrow) dbens());
   if (!h) return DBNET_ENOMEM;
   int rc = ens_guard(nullptr, [&] {
+    AllocStreamScope alloc_stream(cuda_stream);
     if (!out || !graph || !base || !log_scale_init || !options || !enkf)
       raise(DBNET_EINVAL, "NULL argument");
     if (n_members < 2) raise(DBNET_EINVAL, "an ensemble needs at least 2 members");
@@ -344,7 +345,7 @@ int ens_create(const dbnet_graph_t* graph, const dbnet_region_params_t* base, in
     check_enkf(*enkf);
     const int R = graph->n_regions;
     if (R < 1) raise(DBNET_EINVAL, "n_regions must be >= 1");
-    for (int r = 0; r < R; ++r) check_params(base[r], options->dt_ms);
+    for (int r = 0; r < R; ++r) check_params(base[r], options->dt_ms, bin_lead(*options));
     const int M = n_members;
     for (int64_t i = 0; i < (int64_t)M * R * 2; ++i)
       if (!std::isfinite(log_scale_init[i])) raise(DBNET_EINVAL, "non-finite initial log scale");

@@ -33,6 +33,53 @@ struct Error {
 
 extern thread_local std::string g_last_error;
 
+// The caller's device allocator (dbnet_set_allocator), or none (cudaMalloc).
+// Each allocation keeps the hook it came from, so that it is returned to the
+// same allocator whatever is installed later.
+struct AllocHook {
+  dbnet_alloc_fn alloc = nullptr;
+  dbnet_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+AllocHook current_alloc_hook();
+// The stream handed to the hook: the handle's stream while a handle is
+// being built or destroyed on this thread.
+extern thread_local void* g_alloc_stream;
+struct AllocStreamScope {
+  void* prev;
+  explicit AllocStreamScope(void* s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocStreamScope() { g_alloc_stream = prev; }
+};
+
+// Device memory from the hook when one is installed, else cudaMalloc.
+inline void* dev_alloc(size_t bytes, AllocHook& used, void*& stream_used, const char* what) {
+  const AllocHook h = current_alloc_hook();
+  if (h.alloc) {
+    void* p = h.alloc(bytes, g_alloc_stream, h.ctx);
+    if (!p) raise(DBNET_ENOMEM, std::string("the installed allocator returned NULL for ") +
+                                    std::to_string(bytes) + " bytes of " + what);
+    used = h;
+    stream_used = g_alloc_stream;
+    return p;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    raise(e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,
+          "cudaMalloc of " + std::to_string(bytes) + " bytes of " + what + ": " +
+              cudaGetErrorString(e));
+  }
+  used = AllocHook{};
+  stream_used = nullptr;
+  return p;
+}
+inline void dev_free(void* p, size_t bytes, const AllocHook& used, void* stream_used) {
+  if (!p) return;
+  if (used.free) used.free(p, bytes, stream_used, used.ctx);
+  else cudaFree(p);
+}
+
 // A sub-allocator over one device allocation (first fit, 256-byte granules,
 // neighbours merged on release).  Used by the request server, so that
 // admitting and retiring requests never calls cudaMalloc or cudaFree (the
@@ -42,19 +89,10 @@ class Arena {
   Arena() = default;
   Arena(const Arena&) = delete;
   Arena& operator=(const Arena&) = delete;
-  ~Arena() {
-    if (base_) cudaFree(base_);
-  }
+  ~Arena() { dev_free(base_, (size_t)size_, hook_, hook_stream_); }
   void init(int64_t bytes) {
     bytes = round(bytes);
-    cudaError_t e = cudaMalloc((void**)&base_, (size_t)bytes);
-    if (e != cudaSuccess) {
-      base_ = nullptr;
-      cudaGetLastError();
-      raise(e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,
-            "cudaMalloc of the " + std::to_string(bytes) + "-byte request arena: " +
-                cudaGetErrorString(e));
-    }
+    base_ = static_cast<char*>(dev_alloc((size_t)bytes, hook_, hook_stream_, "the request arena"));
     size_ = bytes;
     free_.reset(bytes);
   }
@@ -79,6 +117,8 @@ class Arena {
   char* base_ = nullptr;
   int64_t size_ = 0, used_ = 0;
   FreeList<int64_t> free_;  // byte offsets
+  AllocHook hook_;
+  void* hook_stream_ = nullptr;
 };
 
 // The arena DevBuf::alloc draws from on this thread (nullptr: cudaMalloc).
@@ -96,14 +136,18 @@ struct DevBuf {
   T* p = nullptr;
   int64_t n = 0;
   Arena* ar = nullptr;
+  AllocHook hk;        // the allocator the memory came from (none: cudaMalloc)
+  void* hk_stream = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), ar(o.ar) { o.p = nullptr; o.n = 0; o.ar = nullptr; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n), ar(o.ar), hk(o.hk), hk_stream(o.hk_stream) {
+    o.p = nullptr; o.n = 0; o.ar = nullptr;
+  }
   DevBuf& operator=(DevBuf&& o) noexcept {
     if (this != &o) {
       reset();
-      p = o.p; n = o.n; ar = o.ar;
+      p = o.p; n = o.n; ar = o.ar; hk = o.hk; hk_stream = o.hk_stream;
       o.p = nullptr; o.n = 0; o.ar = nullptr;
     }
     return *this;
@@ -120,19 +164,13 @@ struct DevBuf {
       n = count;
       return;
     }
-    cudaError_t e = cudaMalloc((void**)&p, bytes);
-    if (e != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      raise(e == cudaErrorMemoryAllocation ? DBNET_ENOMEM : DBNET_ECUDA,
-            "cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
-    }
+    p = static_cast<T*>(dev_alloc(bytes, hk, hk_stream, "device state"));
     n = count;
   }
   void reset() {
     if (p) {
       if (ar) ar->give(p, (int64_t)(sizeof(T) * (size_t)n));
-      else cudaFree(p);
+      else dev_free(p, sizeof(T) * (size_t)n, hk, hk_stream);
     }
     p = nullptr;
     n = 0;
@@ -155,7 +193,12 @@ struct GraphDev {
   bool two_w = false;  // a second weight per edge (8-byte records)
   int32_t max_delay = 1, kin_max = 0;
   double w_max = 0.0;
+  // the smallest delay from which every delay carries fewer than
+  // kEmitSegEdges edges per row on average (estimated on a sample of rows),
+  // or 0 when there is none: those short segments are handed on at emission
+  int32_t emit_from = 0;
 };
+constexpr double kEmitSegEdges = 4.0;
 
 struct InstSpec {
   std::shared_ptr<GraphDev> graph;
@@ -189,7 +232,8 @@ struct Engine {
   std::vector<InstHost> inst;
   DevBuf<float> V, J, Ibg, fext;
   DevBuf<uint8_t> ref;
-  DevBuf<int2> acc;
+  DevBuf<int2> acc;        // [acc_slots][stride] accumulators
+  DevBuf<uint16_t> slot_emit;
   DevBuf<InstDesc> desc;
   DevBuf<InstDyn> dyn;
   DevBuf<int4> tile_info;
@@ -214,6 +258,17 @@ struct Engine {
   int tune_done = 0;                  // steps timed so far
   std::vector<int> tune_grid;         // candidates
   std::vector<double> tune_ms;        // summed delivery time per candidate
+  // emission threshold: the engine's current d_emit (D + 1: none) and the
+  // candidate the tuner weighs against "none" (0: no ring, nothing to tune).
+  // Each candidate runs kEmitWarm + kEmitTimed steps (D of them for the
+  // spikes in flight to pass), the last kEmitTimed timed as whole steps.
+  static constexpr int kEmitTimed = 64;
+  int32_t emit_cand = 0;
+  int emit_phase = 0;                 // 0, 1: timing none / the candidate; 2: done
+  int64_t emit_steps = 0;             // steps run in the current phase
+  double emit_ms[2] = {0.0, 0.0};
+  cudaEvent_t emit_ev[2] = {nullptr, nullptr};
+  void set_emit(int32_t d);
   int32_t n_tiles = 0, total_R = 0, shift_S = 16;  // extents the kernels cover
   int64_t stride = 0;
   int32_t cap_tiles = 0, cap_R = 0, cap_inst = 0;    // capacities
@@ -232,9 +287,12 @@ struct Engine {
   // any_ext: launch the update variant with the OU current and the
   // per-neuron injected-current factors; four: four accumulator channels
   // per neuron, so that instances may carry two weights per edge.
+  // emit_from: delays >= it may be handed on at emission (0: never; the
+  // accumulators then have one slot).
   void init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D,
                  const dbnet_options_t& common, void* user_stream, bool any_ext,
-                 bool four = false);
+                 bool four = false, int32_t emit_from = 0);
+  int64_t tune_emit(int64_t n);
   // Put instance k on tiles [first_tile, +tiles of its graph) and region
   // slots [rbase, +R): its constants, buffers and initial state; its step 0
   // is the next iteration enqueued, and it stops after n_end steps.
@@ -256,7 +314,9 @@ struct Engine {
 };
 
 std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s);
-void check_params(const dbnet_region_params_t& p, double dt);
+// min_ref: the fewest refractory steps a region may have (spike binning)
+void check_params(const dbnet_region_params_t& p, double dt, int32_t min_ref);
+int32_t bin_lead(const dbnet_options_t& o);
 void check_options(const dbnet_options_t& o);
 RegionConst region_const(const dbnet_region_params_t& p, double dt, int S, int32_t start,
                          int32_t end, int32_t exc_end);

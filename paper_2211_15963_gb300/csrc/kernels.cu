@@ -53,6 +53,127 @@ __device__ __forceinline__ int find_region(const int32_t* __restrict__ ro, int R
   return lo;
 }
 
+// Edge records stream through the delivery once (a spike's row is read in a
+// few short segments, one per delay, spread over up to D steps), while the
+// accumulators of the step are its working set: the record loads carry an
+// L2 evict-first policy and the accumulator reductions an evict-last one
+// (PTX createpolicy / .L2::cache_hint).
+#ifndef DBNET_L2_HINTS
+#define DBNET_L2_HINTS 1
+#endif
+// 32-edge chunks of a warp's walk whose record loads are issued before the
+// first of their atomics (memory-level parallelism of the walk).
+#ifndef DBNET_WALK_CHUNKS
+#define DBNET_WALK_CHUNKS 4
+#endif
+constexpr int kWalkU = DBNET_WALK_CHUNKS;
+constexpr int kSegGroup = 32;  // spikes per transposition group of the segment-ring copy
+
+__device__ __forceinline__ unsigned long long l2_policy_first() {
+  unsigned long long p = 0;
+#if DBNET_L2_HINTS
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+#endif
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_last() {
+  unsigned long long p = 0;
+#if DBNET_L2_HINTS
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+#endif
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t* a, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ uint2 ld_stream_u64(const uint2* a, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  uint2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ void red_add_s32(int* a, int v, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  asm volatile("red.global.add.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol));
+#else
+  (void)pol;
+  atomicAdd(a, v);
+#endif
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long* a, unsigned long long v,
+                                            unsigned long long pol) {
+#if DBNET_L2_HINTS
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol));
+#else
+  (void)pol;
+  atomicAdd(a, v);
+#endif
+}
+
+// Neuron state: streamed once per step (evict-first) when it is larger than
+// the L2, kept (evict-last) when the whole state fits beside the delivery's
+// working set, so that consecutive steps find it in the L2.
+__device__ __forceinline__ unsigned long long l2_policy_state(int resident) {
+  unsigned long long p = 0;
+#if DBNET_L2_HINTS
+  if (resident) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+#else
+  (void)resident;
+#endif
+  return p;
+}
+__device__ __forceinline__ float4 ld_state_f4(const float* a, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  float4 v;
+  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldcs(reinterpret_cast<const float4*>(a));
+#endif
+}
+__device__ __forceinline__ uint32_t ld_state_u32(const void* a, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  uint32_t v;
+  asm("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldcs(reinterpret_cast<const unsigned int*>(a));
+#endif
+}
+__device__ __forceinline__ void st_state_f4(float* a, float4 v, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+#else
+  (void)pol;
+  __stcs(reinterpret_cast<float4*>(a), v);
+#endif
+}
+__device__ __forceinline__ void st_state_u32(void* a, uint32_t v, unsigned long long pol) {
+#if DBNET_L2_HINTS
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+#else
+  (void)pol;
+  __stcs(reinterpret_cast<unsigned int*>(a), v);
+#endif
+}
+
 // Forward-Euler step of the hemodynamic model for one region (FP64).
 __device__ double bw_euler(double* x, double z, const InstDesc& d) {
   const double s = x[0], f = x[1], v = x[2], q = x[3];
@@ -99,10 +220,13 @@ __global__ void __launch_bounds__(kUpdThreads) k_init_state(EngineDev e, int ins
     *reinterpret_cast<float4*>(e.J + u * e.stride + gi0) = make_float4(0.f, 0.f, 0.f, 0.f);
   *reinterpret_cast<uint32_t*>(e.ref + gi0) = 0u;
   // accumulators: int2 per neuron, or int4 (acc[2i], acc[2i + 1]) with four
-  // channels
+  // channels, in every slot of the ring
   const int words = e.four ? 4 : 2;
-  for (int k = 0; k < words; ++k)
-    *reinterpret_cast<int4*>(e.acc + (e.four ? 2 : 1) * gi0 + 2 * k) = make_int4(0, 0, 0, 0);
+  for (int a = 0; a < e.acc_slots; ++a) {
+    int2* slot = e.acc + (size_t)a * (size_t)e.stride * (e.four ? 2 : 1);
+    for (int k = 0; k < words; ++k)
+      *reinterpret_cast<int4*>(slot + (e.four ? 2 : 1) * gi0 + 2 * k) = make_int4(0, 0, 0, 0);
+  }
 }
 
 __device__ __forceinline__ unsigned long long step_of(const StepRef& sr) {
@@ -167,25 +291,31 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   const int64_t gi0 = (int64_t)tile * kTile + threadIdx.x * 4;
   // (state is streamed once per step: evict-first, so that the delivery's
   // working set keeps the L2)
-  const float4 V4 = __ldcs(reinterpret_cast<const float4*>(e.V + gi0));
+  const unsigned long long pol_state = l2_policy_state(e.state_resident);
+  const float4 V4 = ld_state_f4(e.V + gi0, pol_state);
   float4 J4[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) J4[u] = __ldcs(reinterpret_cast<const float4*>(e.J + u * e.stride + gi0));
-  const uchar4 rf = __ldcs(reinterpret_cast<const uchar4*>(e.ref + gi0));
+  for (int u = 0; u < 4; ++u) J4[u] = ld_state_f4(e.J + u * e.stride + gi0, pol_state);
+  const uint32_t rfw = ld_state_u32(e.ref + gi0, pol_state);
+  const uchar4 rf = make_uchar4((unsigned char)rfw, (unsigned char)(rfw >> 8),
+                                (unsigned char)(rfw >> 16), (unsigned char)(rfw >> 24));
   float4 B4 = make_float4(0.f, 0.f, 0.f, 0.f), F4 = make_float4(1.f, 1.f, 1.f, 1.f);
   if (EXT) {
-    B4 = __ldcs(reinterpret_cast<const float4*>(e.Ibg + gi0));
+    B4 = ld_state_f4(e.Ibg + gi0, pol_state);
     F4 = __ldg(reinterpret_cast<const float4*>(e.fext + gi0));
   }
   // this step's arrivals, per channel (AMPA, NMDA, GABA_A, GABA_B) of the
-  // thread's four neurons
+  // thread's four neurons, from the accumulator slot of this iteration
+  const unsigned long long g = step_of(sr);
+  int2* const accs = e.acc + (e.acc_slots > 1 ? (size_t)(g % (unsigned long long)e.acc_slots) : 0) *
+                                 (size_t)e.stride * (FOUR ? 2 : 1);
   int4 A[4];
   if (FOUR) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) A[k] = *reinterpret_cast<const int4*>(e.acc + 2 * gi0 + 2 * k);
+    for (int k = 0; k < 4; ++k) A[k] = *reinterpret_cast<const int4*>(accs + 2 * gi0 + 2 * k);
   } else {
-    const int4 a01 = *reinterpret_cast<const int4*>(e.acc + gi0);
-    const int4 a23 = *reinterpret_cast<const int4*>(e.acc + gi0 + 2);
+    const int4 a01 = *reinterpret_cast<const int4*>(accs + gi0);
+    const int4 a23 = *reinterpret_cast<const int4*>(accs + gi0 + 2);
     A[0] = make_int4(a01.x, a01.x, a01.y, a01.y);
     A[1] = make_int4(a01.z, a01.z, a01.w, a01.w);
     A[2] = make_int4(a23.x, a23.x, a23.y, a23.y);
@@ -193,7 +323,6 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   }
 
   const int4 ti = e.tile_info[tile];  // instance, first region, regions touched
-  const unsigned long long g = step_of(sr);
   if (sr.next && threadIdx.x == 0) *sr.next = g + 1ull;
   if (ti.x < 0) return;  // unused tile
   const int inst = ti.x, r0 = ti.y, nr = ti.z;
@@ -217,7 +346,7 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   if (active && li0 < d.N) {
 #pragma unroll
     for (int k = 0; k < (FOUR ? 4 : 2); ++k)
-      *reinterpret_cast<int4*>(e.acc + (FOUR ? 2 : 1) * gi0 + 2 * k) = make_int4(0, 0, 0, 0);
+      *reinterpret_cast<int4*>(accs + (FOUR ? 2 : 1) * gi0 + 2 * k) = make_int4(0, 0, 0, 0);
     unsigned long long x[4] = {(unsigned long long)n, (unsigned long long)(li0 >> 2), 0ull, 0ull};
     philox4x64_10(x, d.seed, d.net_id);
     float ib[4] = {B4.x, B4.y, B4.z, B4.w};
@@ -305,16 +434,17 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
         v[k] = vn;
       }
     }
-    __stcs(reinterpret_cast<float4*>(e.V + gi0), make_float4(v[0], v[1], v[2], v[3]));
+    st_state_f4(e.V + gi0, make_float4(v[0], v[1], v[2], v[3]), pol_state);
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      __stcs(reinterpret_cast<float4*>(e.J + u * e.stride + gi0),
-             make_float4(j[u][0], j[u][1], j[u][2], j[u][3]));
-    __stcs(reinterpret_cast<uchar4*>(e.ref + gi0),
-           make_uchar4((unsigned char)rr[0], (unsigned char)rr[1], (unsigned char)rr[2],
-                       (unsigned char)rr[3]));
+      st_state_f4(e.J + u * e.stride + gi0, make_float4(j[u][0], j[u][1], j[u][2], j[u][3]),
+                  pol_state);
+    st_state_u32(e.ref + gi0,
+                 (uint32_t)rr[0] | ((uint32_t)rr[1] << 8) | ((uint32_t)rr[2] << 16) |
+                     ((uint32_t)rr[3] << 24),
+                 pol_state);
     if (EXT && (d.ext & kExtOU))
-      __stcs(reinterpret_cast<float4*>(e.Ibg + gi0), make_float4(ib[0], ib[1], ib[2], ib[3]));
+      st_state_f4(e.Ibg + gi0, make_float4(ib[0], ib[1], ib[2], ib[3]), pol_state);
   }
 
   // ---- spikes: one ring append, spike and raster count per block ---------
@@ -328,7 +458,11 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   }
   if (lane == 31) s_wtot[warp] = (uint32_t)ps;
   __syncthreads();
-  const int slot = (int)(g % (unsigned long long)e.D);
+  // the ring slot of the step at which these spikes are handed on: this
+  // step, or with spike binning the last step of its bin
+  const unsigned long long rel =
+      d.bin_sp ? d.g0 + (unsigned long long)((n / d.spb + 1) * d.spb - 1) : g;
+  const int slot = (int)(rel % (unsigned long long)e.D);
   if (threadIdx.x == 0) {
     uint32_t tot = 0;
     for (int w = 0; w < kUpdThreads / 32; ++w) {
@@ -341,6 +475,7 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     s_rbase = d.raster_cap > 0 ? atomicAdd(&e.dyn[inst].raster_count, (unsigned long long)tot) : 0ull;
   }
   __syncthreads();
+  unsigned long long ev = 0;
   if (spk) {
     uint64_t pos = (uint64_t)s_hbase + s_wtot[warp] + (uint32_t)(ps - nsp);
     unsigned long long rpos = s_rbase + s_wtot[warp] + (unsigned long long)(ps - nsp);
@@ -354,6 +489,9 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
         atomicOr(e.flags, kFlagHistOverflow);
       ++pos;
       atomicAdd(&e.cnt[d.rbase + reg[k]], 1);
+      // the spike's synaptic events: its out-degree (Supp. Alg. 2 pushes
+      // every out-edge once), counted as the spike is emitted
+      ev += (unsigned long long)(__ldg(d.row_ptr + li0 + k + 1) - __ldg(d.row_ptr + li0 + k));
       if (d.raster_cap > 0) {
         if (rpos < (unsigned long long)d.raster_cap) {
           d.raster_step[rpos] = (int32_t)n;
@@ -363,6 +501,9 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
       }
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
+  if (lane == 0 && ev) atomicAdd(e.events, ev);
 }
 
 __device__ __forceinline__ uint32_t edge_delay(const uint32_t* col, const uint8_t* dl, int shift,
@@ -380,79 +521,136 @@ __device__ int64_t first_delay_at_least(const uint32_t* col, const uint8_t* dl, 
   return lo;
 }
 
+// Stage one of resolving an item (spike k of the ring slot of step g - d,
+// delay d, due now; or, in the emission range, spike k of step g - 1 and one
+// of its long delays d): everything that needs no other load -- the ring
+// entry and, from the delay-major segment ring, the row start and the two
+// segment counts -- and the accumulator slot its edges go to.
+struct ItemLoads {
+  uint32_t ent, d, slot, k, aslot;
+  int64_t r0;
+  uint32_t a, b;
+  bool ring;
+};
+
 // FOUR: the engine keeps four accumulator channels per neuron; an edge adds
 // its two weights (the one weight twice for one-weight records) to the
 // channel pair of the source's class with one 64-bit atomic.  Every channel
 // sum stays below 2^31 (the fixed-point scale is chosen so), so the low word
-// never carries into the high one.
-template <bool FOUR>
-__global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr) {
+// never carries into the high one.  SINGLE: the engine holds one instance
+// (a network, or the allocation-free run), so every spike's descriptor is
+// the first.
+template <bool FOUR, bool SINGLE>
+__global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef sr) {
   __shared__ unsigned long long s_pre[256];  // items whose delay is below index + 1
   __shared__ unsigned long long s_wsum[kDelThreads / 32];
   __shared__ unsigned long long s_total;
+  __shared__ __align__(16) uint16_t s_tab[256 * kSegGroup];  // [delay][spike] of a copy group
+  __shared__ const uint4* s_row[kSegGroup];
+  __shared__ int32_t s_nq[kSegGroup];
+  __shared__ long long s_r0[kSegGroup];
   const unsigned long long g = step_of(sr);
   const int D = e.D;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   // close the bin that ended with the previous iteration, one region per thread
   for (int gr = gtid; gr < e.total_R; gr += gridDim.x * blockDim.x) close_region(e, gr, g);
-  // the slot this iteration's update will fill was last read by the previous one
-  if (gtid == 0) e.hcount[g % (unsigned long long)D] = 0u;
+  // the slot that the updates from this iteration on fill (a bin later with
+  // spike binning) was last read by the previous iteration; the slot handed
+  // on at g - 1 gets its long delays now, at emission, when d_emit allows
+  const unsigned long long s1 = (g + (unsigned long long)D - 1ull) % (unsigned long long)D;
+  if (gtid == 0) {
+    e.hcount[(g + (unsigned long long)e.bin_lead) % (unsigned long long)D] = 0u;
+    if (e.slot_emit) e.slot_emit[s1] = (uint16_t)e.d_emit;
+  }
   // The leading nA blocks copy the row start and segment counts of the
-  // previous step's spikes into the delay-major ring (thread per spike, so
-  // each store of a delay plane is coalesced across the warp) and take no
-  // items; nA follows that step's spike count, the same in every block.
+  // previous step's spikes into the delay-major ring and take no items; nA
+  // follows that step's spike count, the same in every block.
   unsigned long long c1 = 0;
   int nA = 0;
-  const unsigned long long s1 = (g + (unsigned long long)D - 1ull) % (unsigned long long)D;
-  if (e.seg_cap > 0 && g >= 1ull) {
+  // delay-major planes the later arrival items read: delays below d_emit
+  const int planes = e.dcap < e.d_emit - 1 ? e.dcap : e.d_emit - 1;
+  if (e.seg_cap > 0 && g >= 1ull && planes > 1) {
     c1 = e.hcount[s1];
     if (c1 > (unsigned long long)e.hist_cap) c1 = (unsigned long long)e.hist_cap;
     if (c1 > (unsigned long long)e.seg_cap) c1 = (unsigned long long)e.seg_cap;
-    const unsigned long long want = (c1 + kDelThreads - 1) / kDelThreads;
+    const unsigned long long want = (c1 + kSegGroup - 1) / kSegGroup;
     const int most = gridDim.x >= 16 ? (int)gridDim.x / 8 : 1;  // the host launches >= 2 blocks
     nA = want < (unsigned long long)most ? (int)want : most;
   }
   if ((int)blockIdx.x < nA) {
+    // Groups of 32 spikes: their segment-table rows are loaded at once (one
+    // 16-byte vector of 8 delays per task, consecutive lanes on consecutive
+    // spikes), transposed in shared memory to [delay][spike], and stored
+    // plane by plane, 64 contiguous bytes per delay.
     const size_t cap = (size_t)e.seg_cap;
-    for (unsigned long long k = gtid; k < c1; k += (unsigned long long)nA * kDelThreads) {
-      const uint32_t ent = e.hist[s1 * (unsigned long long)e.hist_cap + k];
-      const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
-      const int inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
-      if (inst < 0) continue;  // never for a listed spike: tiles are reused D steps late
-      const InstDesc& dd = e.insts[inst];
-      if (dd.seg_kind != kSeg16) continue;
-      const int64_t j = gidx - dd.base;
-      e.hr0[s1 * cap + k] = __ldg(dd.row_ptr + j);
-      const uint4* T = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(dd.seg) +
-                                                      j * dd.seg_stride);
-      uint16_t* H = e.hseg + (s1 * (size_t)e.dcap) * cap + k;
-      const int nq = (dd.dmax + 7) >> 3;
-      for (int q0 = 0; q0 < nq; q0 += 4) {
-        uint4 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = q0 + i < nq ? __ldg(T + q0 + i) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t wd[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int dl = (q0 + i) * 8 + u;
-            if (dl < dd.dmax) H[(size_t)dl * cap] = (uint16_t)(wd[u >> 1] >> ((u & 1) * 16));
+    const int dcap = e.dcap;
+    const int nq_all = (planes + 7) >> 3;
+    for (unsigned long long k0 = (unsigned long long)blockIdx.x * kSegGroup; k0 < c1;
+         k0 += (unsigned long long)nA * kSegGroup) {
+      if (threadIdx.x < kSegGroup) {
+        const unsigned long long k = k0 + threadIdx.x;
+        const uint4* row = nullptr;
+        int nq = 0;
+        long long r0 = 0;
+        if (k < c1) {
+          const uint32_t ent = e.hist[s1 * (unsigned long long)e.hist_cap + k];
+          const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
+          const int inst = SINGLE ? 0 : e.tile_info[gidx / kTile].x;
+          if (inst >= 0) {
+            const InstDesc& dd = e.insts[inst];
+            if (dd.seg_kind == kSeg16) {
+              const int64_t j = gidx - dd.base;
+              r0 = __ldg(dd.row_ptr + j);
+              row = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(dd.seg) +
+                                                   j * dd.seg_stride);
+              nq = (dd.dmax + 7) >> 3;
+            }
           }
         }
+        s_row[threadIdx.x] = row;
+        s_nq[threadIdx.x] = nq;
+        s_r0[threadIdx.x] = r0;
       }
+      __syncthreads();
+      for (int t = threadIdx.x; t < kSegGroup * nq_all; t += kDelThreads) {
+        const int ks = t & (kSegGroup - 1), q = t / kSegGroup;
+        const uint4 v = q < s_nq[ks] ? __ldg(s_row[ks] + q) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          s_tab[(8 * q + i) * kSegGroup + ks] = (uint16_t)(wd[i >> 1] >> ((i & 1) * 16));
+      }
+      __syncthreads();
+      // k0 + 31 < seg_cap (a multiple of 32): whole groups stay in the ring
+      for (int t = threadIdx.x; t < planes * (kSegGroup / 2); t += kDelThreads) {
+        const int dl = t / (kSegGroup / 2), w = t % (kSegGroup / 2);
+        const uint32_t pair = *reinterpret_cast<const uint32_t*>(&s_tab[dl * kSegGroup + 2 * w]);
+        uint32_t* H = reinterpret_cast<uint32_t*>(e.hseg + (s1 * (size_t)dcap + dl) * cap + k0);
+        H[w] = pair;
+      }
+      if (threadIdx.x < kSegGroup) e.hr0[s1 * cap + k0 + threadIdx.x] = s_r0[threadIdx.x];
+      __syncthreads();
     }
     return;
   }
   const int bB = (int)blockIdx.x - nA, nB = (int)gridDim.x - nA;  // item blocks
 
-  // spikes of step g - d for d = threadIdx.x + 1, and their exclusive prefix
+  // spikes handed on at step g - d for d = threadIdx.x + 1, and their
+  // exclusive prefix (delays up to D - 1 - bin_lead: the later slots hold
+  // bins still filling)
+  const int dlim = D - 1 - e.bin_lead;
   unsigned long long c = 0;
   const int dme = threadIdx.x + 1;
-  if (dme < D && g >= (unsigned long long)dme) {
-    const unsigned long long h = e.hcount[(g - dme) % (unsigned long long)D];
-    c = h < (unsigned long long)e.hist_cap ? h : (unsigned long long)e.hist_cap;
+  if (dme <= dlim && g >= (unsigned long long)dme) {
+    const unsigned long long sl = (g - dme) % (unsigned long long)D;
+    // delays at or above the threshold in force when that slot was handed
+    // on went out at emission
+    const int thr = dme == 1 ? e.d_emit : (e.slot_emit ? (int)e.slot_emit[sl] : D + 1);
+    if (dme < thr) {
+      const unsigned long long h = e.hcount[sl];
+      c = h < (unsigned long long)e.hist_cap ? h : (unsigned long long)e.hist_cap;
+    }
   }
   unsigned long long incl = c;
 #pragma unroll
@@ -473,66 +671,115 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
   }
   __syncthreads();
   s_pre[threadIdx.x] = s_wsum[warp] + incl - c;
-  const int nd = D - 1 < kDelThreads ? D - 1 : kDelThreads;  // delay buckets d = 1..nd
-  const unsigned long long W = s_total;
+  const int nd = dlim < kDelThreads ? dlim : kDelThreads;  // delay buckets d = 1..nd
+  // the emission range: every spike handed on at g - 1 times its delays
+  // d_emit..dlim, spike-major so that consecutive lanes take consecutive
+  // delays of one row (its segments lie end to end)
+  const unsigned long long W_arr = s_total;
+  const int ne = e.d_emit <= dlim ? dlim - e.d_emit + 1 : 0;
+  unsigned long long c1e = 0;
+  if (ne > 0 && g >= 1ull) {
+    c1e = e.hcount[s1];
+    if (c1e > (unsigned long long)e.hist_cap) c1e = (unsigned long long)e.hist_cap;
+  }
+  const unsigned long long W = W_arr + c1e * (unsigned long long)ne;
+  const unsigned long long acc_elems = (unsigned long long)e.stride * (FOUR ? 2 : 1);
+  const uint32_t aslot_now = e.acc_slots > 1 ? (uint32_t)(g % (unsigned long long)e.acc_slots) : 0u;
   __syncthreads();
 
-  unsigned long long ev = 0;
-  const unsigned long long wstride = (unsigned long long)nB * blockDim.x;
-  const unsigned long long wbase = (unsigned long long)bB * blockDim.x + warp * 32;
-  for (unsigned long long b0 = wbase; b0 < W; b0 += wstride) {  // warp-uniform
-    // each lane resolves one item: (spike, delay) -> its edge segment
-    const unsigned long long t = b0 + lane;
-    int64_t e0 = 0;
-    uint32_t nseg = 0;
-    int inst = 0;
-    uint32_t cls = 0;
-    if (t < W) {
-      // bucket: the largest i with s_pre[i] <= t; delay d = i + 1
-      int lo = 0, hi = nd - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_pre[mid] <= t) lo = mid; else hi = mid - 1;
-      }
-      uint32_t d = (uint32_t)lo + 1u;
-      const unsigned long long k = t - s_pre[lo];
-      const unsigned long long slot = (g - d) % (unsigned long long)D;
-      const uint32_t ent = e.hist[slot * (unsigned long long)e.hist_cap + k];
-      const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
-      cls = ent >> 31;
-      inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
-      if (inst < 0) inst = 0, d = 0u;  // (as above) -- takes no edges
-      const InstDesc& dd = e.insts[inst];
-      if (d >= 1u && (int32_t)d <= dd.dmax) {
-        const int64_t j = gidx - dd.base;
-        int64_t r0, a, b;
-        if (dd.seg_kind == kSeg16 && d >= 2u && k < (unsigned long long)e.seg_cap) {
-          // from the delay-major ring (consecutive lanes, consecutive spikes)
-          const size_t cap = (size_t)e.seg_cap;
-          r0 = __ldg(e.hr0 + slot * cap + k);
-          const uint16_t* H = e.hseg + (slot * (size_t)e.dcap) * cap + k;
-          a = (int64_t)__ldg(H + (size_t)(d - 2u) * cap);
-          b = (int64_t)__ldg(H + (size_t)(d - 1u) * cap);
-        } else if (dd.seg_kind == kSeg16) {
-          r0 = __ldg(dd.row_ptr + j);
-          const uint16_t* T = static_cast<const uint16_t*>(dd.seg) + j * dd.seg_stride;
-          a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
-          b = (int64_t)__ldg(T + d - 1);
-        } else if (dd.seg_kind == kSeg32) {
-          r0 = __ldg(dd.row_ptr + j);
-          const uint32_t* T = static_cast<const uint32_t*>(dd.seg) + j * dd.seg_stride;
-          a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
-          b = (int64_t)__ldg(T + d - 1);
-        } else {
-          r0 = __ldg(dd.row_ptr + j);
-          const int64_t r1 = __ldg(dd.row_ptr + j + 1);
-          a = first_delay_at_least(dd.col, dd.delay, dd.shift, r0, r1, d) - r0;
-          b = first_delay_at_least(dd.col, dd.delay, dd.shift, r0 + a, r1, d + 1) - r0;
-        }
-        nseg = (uint32_t)(b - a);
-        e0 = r0 + a;
+  const unsigned long long pol_rec = l2_policy_first(), pol_acc = l2_policy_last();
+  const size_t cap = (size_t)e.seg_cap;
+  // stage one: bucket (delay) by binary search over the prefix, then the
+  // loads that need nothing else
+  auto stage_one = [&](unsigned long long t, ItemLoads& p) {
+    p.d = 0u;
+    p.ring = false;
+    if (t >= W) return;
+    if (t >= W_arr) {  // emission: spike k of step g - 1, delay d, into slot g - 1 + d
+      const unsigned long long te = t - W_arr;
+      p.k = (uint32_t)(te / (unsigned long long)ne);
+      p.d = (uint32_t)e.d_emit + (uint32_t)(te % (unsigned long long)ne);
+      p.slot = (uint32_t)s1;
+      p.aslot = (uint32_t)((g - 1ull + p.d) % (unsigned long long)e.acc_slots);
+      p.ent = __ldg(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
+      return;
+    }
+    p.aslot = aslot_now;
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_pre[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    p.d = (uint32_t)lo + 1u;
+    p.k = (uint32_t)(t - s_pre[lo]);
+    p.slot = (uint32_t)((g - p.d) % (unsigned long long)D);
+    p.ent = __ldg(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
+    if (p.d >= 2u && p.k < cap) {  // from the delay-major ring (coalesced across lanes)
+      p.ring = true;
+      p.r0 = __ldg(e.hr0 + p.slot * cap + p.k);
+      const uint16_t* H = e.hseg + ((size_t)p.slot * (size_t)e.dcap) * cap + p.k;
+      p.a = __ldg(H + (size_t)(p.d - 2u) * cap);
+      p.b = __ldg(H + (size_t)(p.d - 1u) * cap);
+    }
+  };
+  // stage two: the item's edge segment [e0, e0 + nseg) from the stage-one
+  // loads, or by the graph's own tables when the ring does not hold it
+  auto stage_two = [&](const ItemLoads& p, int64_t& e0, uint32_t& nseg, int& inst, uint32_t& cls) {
+    e0 = 0;
+    nseg = 0u;
+    inst = 0;
+    cls = 0u;
+    if (p.d == 0u) return;
+    cls = p.aslot << 1;  // the accumulator slot travels with the class bit
+    const int64_t gidx = (int64_t)(p.ent & 0x7FFFFFFFu);
+    cls |= p.ent >> 31;
+    if (!SINGLE) {
+      inst = e.tile_info[gidx / kTile].x;
+      if (inst < 0) {  // never for a listed spike: tiles are reused D steps late
+        inst = 0;
+        return;
       }
     }
+    const InstDesc& dd = e.insts[inst];
+    const uint32_t d = p.d;
+    if ((int32_t)d > dd.dmax) return;
+    const int64_t j = gidx - dd.base;
+    int64_t r0, a, b;
+    if (dd.seg_kind == kSeg16 && p.ring) {
+      r0 = p.r0;
+      a = (int64_t)p.a;
+      b = (int64_t)p.b;
+    } else if (dd.seg_kind == kSeg16) {
+      r0 = __ldg(dd.row_ptr + j);
+      const uint16_t* T = static_cast<const uint16_t*>(dd.seg) + j * dd.seg_stride;
+      a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
+      b = (int64_t)__ldg(T + d - 1);
+    } else if (dd.seg_kind == kSeg32) {
+      r0 = __ldg(dd.row_ptr + j);
+      const uint32_t* T = static_cast<const uint32_t*>(dd.seg) + j * dd.seg_stride;
+      a = d >= 2 ? (int64_t)__ldg(T + d - 2) : 0;
+      b = (int64_t)__ldg(T + d - 1);
+    } else {
+      r0 = __ldg(dd.row_ptr + j);
+      const int64_t r1 = __ldg(dd.row_ptr + j + 1);
+      a = first_delay_at_least(dd.col, dd.delay, dd.shift, r0, r1, d) - r0;
+      b = first_delay_at_least(dd.col, dd.delay, dd.shift, r0 + a, r1, d + 1) - r0;
+    }
+    nseg = (uint32_t)(b - a);
+    e0 = r0 + a;
+  };
+
+  const unsigned long long wstride = (unsigned long long)nB * blockDim.x;
+  const unsigned long long wbase = (unsigned long long)bB * blockDim.x + warp * 32;
+  ItemLoads pend;
+  stage_one(wbase + lane, pend);
+  for (unsigned long long b0 = wbase; b0 < W; b0 += wstride) {  // warp-uniform
+    int64_t e0;
+    uint32_t nseg, cls;
+    int inst;
+    stage_two(pend, e0, nseg, inst, cls);
+    // the next batch's loads fly while this batch's edges are walked
+    stage_one(b0 + wstride + lane, pend);
     // the warp's segments laid end to end; consecutive lanes take
     // consecutive edges (coalesced), the owning item found by a shuffle search
     uint32_t incl = nseg;
@@ -543,61 +790,72 @@ __global__ void __launch_bounds__(kDelThreads) k_deliver(EngineDev e, StepRef sr
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
     const uint32_t ex = incl - nseg;
-    for (uint32_t f = 0; f < total; f += 32) {  // warp-uniform
-      const uint32_t fi = f + lane;
-      int L = 0;
+    // instance (23 bits) | accumulator slot << 23 (8 bits) | class << 31
+    const int icls = inst | (int)((cls >> 1) << 23) | (int)((cls & 1u) << 31);
+    for (uint32_t f = 0; f < total; f += 32u * kWalkU) {  // warp-uniform
+      uint32_t tg[kWalkU], wv[kWalkU];
+      int ic[kWalkU];
+      bool ok[kWalkU];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = L + step < 32 ? L + step : 31;
-        const uint32_t v = __shfl_sync(kFull, ex, cand);
-        if (L + step < 32 && v <= fi) L = cand;
-      }
-      const int64_t q0 = __shfl_sync(kFull, e0, L);
-      const uint32_t qx = __shfl_sync(kFull, ex, L);
-      const int qi = __shfl_sync(kFull, inst, L);
-      const uint32_t qc = __shfl_sync(kFull, cls, L);
-      if (fi < total) {
-        const InstDesc& dd = e.insts[qi];
-        const int64_t ei = q0 + (int64_t)(fi - qx);
-        uint32_t tg, wb, wb2 = 0;
-        if (FOUR && dd.two_w) {  // 8-byte record: target, weight | second weight << 16
-          const uint2 r4 = __ldg(reinterpret_cast<const uint2*>(dd.rec) + ei);
-          tg = r4.x;
-          wb = r4.y & 0xFFFFu;
-          wb2 = r4.y >> 16;
-        } else if (dd.rec) {
-          const uint16_t* r3 = dd.rec + 3 * ei;
-          tg = (uint32_t)__ldg(r3) | ((uint32_t)__ldg(r3 + 1) << 16);
-          wb = __ldg(r3 + 2);
-          wb2 = wb;
-        } else {
-          tg = __ldg(dd.col + ei) & dd.tmask;
-          wb = __ldg(dd.w + ei);
-          wb2 = wb;
+      for (int u = 0; u < kWalkU; ++u) {
+        ok[u] = false;
+        if (f + 32u * u < total) {  // warp-uniform
+          const uint32_t fi = f + 32u * u + lane;
+          int L = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int cand = L + step < 32 ? L + step : 31;
+            const uint32_t v = __shfl_sync(kFull, ex, cand);
+            if (L + step < 32 && v <= fi) L = cand;
+          }
+          const int64_t q0 = __shfl_sync(kFull, e0, L);
+          const uint32_t qx = __shfl_sync(kFull, ex, L);
+          ic[u] = __shfl_sync(kFull, icls, L);
+          if (fi < total) {
+            const InstDesc& dd = e.insts[SINGLE ? 0 : (ic[u] & 0x7FFFFF)];
+            const int64_t ei = q0 + (int64_t)(fi - qx);
+            if (FOUR && dd.two_w) {  // 8-byte record: target, weight | second weight << 16
+              const uint2 r4 = ld_stream_u64(reinterpret_cast<const uint2*>(dd.rec) + ei, pol_rec);
+              tg[u] = r4.x;
+              wv[u] = r4.y;
+            } else if (dd.rec) {
+              // 6-byte record at byte 6 ei: two aligned words cover it (the
+              // record array carries 8 bytes of padding at its end)
+              const size_t byte = 6 * (size_t)ei;
+              const uint32_t* w4 = reinterpret_cast<const uint32_t*>(
+                  reinterpret_cast<const unsigned char*>(dd.rec) + (byte & ~size_t(3)));
+              const uint32_t w0 = ld_stream_u32(w4, pol_rec), w1 = ld_stream_u32(w4 + 1, pol_rec);
+              const uint32_t sh = (uint32_t)(byte & 3u) * 8u;  // 0 or 16
+              tg[u] = __funnelshift_r(w0, w1, sh);
+              const uint32_t wb = (w1 >> sh) & 0xFFFFu;
+              wv[u] = wb | (wb << 16);
+            } else {
+              tg[u] = __ldg(dd.col + ei) & dd.tmask;
+              const uint32_t wb = __ldg(dd.w + ei);
+              wv[u] = wb | (wb << 16);
+            }
+            ok[u] = true;
+          }
         }
-        const int q = __float2int_rn(__fmul_rn(__uint_as_float(wb << 16), dd.two_S));
+      }
+#pragma unroll
+      for (int u = 0; u < kWalkU; ++u) {
+        if (!ok[u]) continue;
+        const InstDesc& dd = e.insts[SINGLE ? 0 : (ic[u] & 0x7FFFFF)];
+        const uint32_t qc = (uint32_t)ic[u] >> 31;
+        int2* const accs = e.acc + (size_t)(((uint32_t)ic[u] >> 23) & 0xFFu) * acc_elems;
+        const int q = __float2int_rn(__fmul_rn(__uint_as_float(wv[u] << 16), dd.two_S));
         if (FOUR) {
-          const int q2 = __float2int_rn(__fmul_rn(__uint_as_float(wb2 << 16), dd.two_S));
-          unsigned long long* accp = reinterpret_cast<unsigned long long*>(e.acc) +
-                                     2 * (size_t)(dd.base + (int64_t)tg) + qc;
-          atomicAdd(accp, ((unsigned long long)(uint32_t)q2 << 32) | (uint32_t)q);
+          const int q2 = __float2int_rn(__fmul_rn(__uint_as_float(wv[u] & 0xFFFF0000u), dd.two_S));
+          unsigned long long* accp = reinterpret_cast<unsigned long long*>(accs) +
+                                     2 * (size_t)(dd.base + (int64_t)tg[u]) + qc;
+          red_add_u64(accp, ((unsigned long long)(uint32_t)q2 << 32) | (uint32_t)q, pol_acc);
         } else {
-          int* accp = reinterpret_cast<int*>(e.acc + dd.base) + qc;
-          atomicAdd(accp + 2 * (size_t)tg, q);
+          int* accp = reinterpret_cast<int*>(accs + dd.base) + qc;
+          red_add_s32(accp + 2 * (size_t)tg[u], q, pol_acc);
         }
       }
     }
-    if (lane == 0) ev += total;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
-  __syncthreads();
-  if (lane == 0) s_wsum[warp] = ev;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long s = 0;
-    for (int w = 0; w < kDelThreads / 32; ++w) s += s_wsum[w];
-    if (s) atomicAdd(e.events, s);
   }
 }
 
@@ -732,7 +990,7 @@ int deliver_grid() {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deliver<false>, kDelThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deliver<false, true>, kDelThreads, 0);
     if (occ < 1) occ = 1;
     g_deliver_grid = sms * occ;
   }
@@ -741,8 +999,13 @@ int deliver_grid() {
 
 void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s) {
   if (grid < 2) grid = 2;  // with a segment ring, block 0 may take no items
-  if (e.four) k_deliver<true><<<grid, kDelThreads, 0, s>>>(e, sr);
-  else k_deliver<false><<<grid, kDelThreads, 0, s>>>(e, sr);
+  if (e.n_inst == 1) {
+    if (e.four) k_deliver<true, true><<<grid, kDelThreads, 0, s>>>(e, sr);
+    else k_deliver<false, true><<<grid, kDelThreads, 0, s>>>(e, sr);
+  } else {
+    if (e.four) k_deliver<true, false><<<grid, kDelThreads, 0, s>>>(e, sr);
+    else k_deliver<false, false><<<grid, kDelThreads, 0, s>>>(e, sr);
+  }
 }
 
 void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,

@@ -182,8 +182,10 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
       if (graph->n_exc[r] < 0 || graph->n_exc[r] > ro[r + 1] - ro[r]) raise(DBNET_EINVAL, "n_exc out of range");
     }
     check_options(*options);
+    if (options->bin_spikes)
+      raise(DBNET_EUNSUPPORTED, "the allocation-free entry point hands every spike on in its own step");
     for (int32_t r = 0; r < R; ++r) {
-      check_params(params[r], options->dt_ms);
+      check_params(params[r], options->dt_ms, 0);
       if (params[r].ou_mu != 0.0 || params[r].ou_sigma != 0.0 || params[r].iext_shape != 0.0)
         raise(DBNET_EUNSUPPORTED,
               "the allocation-free entry point has no OU state or injected-current factors");
@@ -303,6 +305,9 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     e.ref = ref;
     e.acc = reinterpret_cast<int2*>(at(kOffAcc));
     e.stride = n_pad;
+    e.acc_slots = 1;
+    e.d_emit = dmax + 2;  // every delay at arrival time
+    e.slot_emit = nullptr;
     e.insts = reinterpret_cast<const InstDesc*>(at(kOffDesc));
     e.dyn = reinterpret_cast<InstDyn*>(at(kOffDyn));
     e.tile_info = reinterpret_cast<const int4*>(at(kOffTiles));

@@ -397,6 +397,7 @@ int dbsrv_create(const dbsrv_options_t* options, void* cuda_stream, dbsrv_t** ou
   *out = nullptr;
   auto s = std::make_unique<dbsrv>();
   int rc = srv_guard(nullptr, [&] {
+    AllocStreamScope alloc_stream(cuda_stream);
     const dbsrv_options_t& o = *options;
     check_options(o.run);
     if (o.max_neurons < 1 || o.max_requests < 1 || o.max_regions < 1 || o.chunk_steps < 1 ||
@@ -408,7 +409,7 @@ int dbsrv_create(const dbsrv_options_t* options, void* cuda_stream, dbsrv_t** ou
     if (tiles * kTile >= (int64_t(1) << 31)) raise(DBNET_EINVAL, "max_neurons too large");
     s->opt = o;
     s->eng.reset(new Engine());
-    s->eng->init_pool(o.max_requests, tiles, o.max_regions, o.max_delay + 1, o.run, cuda_stream,
+    s->eng->init_pool(o.max_requests, tiles, o.max_regions, o.max_delay + 1 + bin_lead(o.run), o.run, cuda_stream,
                       true,  // any request may bring the OU current
                       o.two_weights != 0);
     s->eng->set_extent(1, 1);
@@ -438,7 +439,7 @@ int dbsrv_submit(dbsrv_t* s, const dbnet_graph_t* graph, const dbnet_region_para
       raise(DBNET_ERANGE, "the request is larger than the server's pool");
     if (g.weight2 && !s->opt.two_weights)
       raise(DBNET_EUNSUPPORTED, "two weights per edge need a server created with two_weights = 1");
-    for (int32_t r = 0; r < R; ++r) check_params(params[r], s->opt.run.dt_ms);
+    for (int32_t r = 0; r < R; ++r) check_params(params[r], s->opt.run.dt_ms, bin_lead(s->opt.run));
     auto q = std::make_unique<Req>();
     q->id = s->next_id++;
     q->graph = g;

@@ -37,6 +37,15 @@ DBENS_GLOBAL = 1
 _d, _i32, _i64, _u64, _vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
 
 
+dbnet_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+dbnet_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                 ctypes.c_void_p)
+
+
+class dbnet_allocator_t(ctypes.Structure):
+    _fields_ = [("alloc", dbnet_alloc_fn), ("free", dbnet_free_fn), ("ctx", ctypes.c_void_p)]
+
+
 class dbnet_graph_t(ctypes.Structure):
     _fields_ = [("n_neurons", _i32), ("n_regions", _i32), ("region_offsets", _vp),
                 ("n_exc", _vp), ("row_ptr", _vp), ("col", _vp), ("weight", _vp),
@@ -55,7 +64,8 @@ class dbnet_options_t(ctypes.Structure):
                 ("bw_kappa", _d), ("bw_gamma", _d), ("bw_tau", _d), ("bw_alpha", _d),
                 ("bw_rho", _d), ("bw_V0", _d), ("seed", _u64), ("net_id", _u64),
                 ("fixed_shift", _i32), ("precision", _i32), ("raster_capacity", _i64),
-                ("bold_capacity", _i64), ("autotune_at", _i64)]
+                ("bold_capacity", _i64), ("autotune_at", _i64), ("bin_spikes", _i32),
+                ("emit_delay", _i32)]
 
 
 class dbnet_stats_t(ctypes.Structure):
@@ -63,7 +73,7 @@ class dbnet_stats_t(ctypes.Structure):
                 ("raster_dropped", _i64), ("bold_samples", _i64), ("fixed_shift", _i32),
                 ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32),
                 ("deliver_blocks", _i32), ("autotuned", _i32), ("two_weights", _i32),
-                ("reserved", _i32)]
+                ("seg_ring", _i32), ("emit_delay", _i32), ("reserved", _i32)]
 
 
 class dbnet_device_graph_t(ctypes.Structure):
@@ -111,6 +121,7 @@ DBENS_T_NONE = -1
 _SIGS = {
     "dbnet_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dbnet_last_error": (ctypes.c_char_p, []),
+    "dbnet_set_allocator": (ctypes.c_int, [ctypes.POINTER(dbnet_allocator_t)]),
     "dbnet_abi_sizes": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dbnet_options_default": (ctypes.c_int, [ctypes.POINTER(dbnet_options_t)]),
     "dbnet_create": (ctypes.c_int, [ctypes.POINTER(dbnet_graph_t), _vp,
@@ -221,6 +232,50 @@ def _stream(stream) -> int:
     if hasattr(stream, "cuda_stream"):
         return int(stream.cuda_stream)
     return int(stream)
+
+
+# ------------------------------------------------------------- allocator ----
+_allocators = []   # installed callbacks stay alive for the handles that used them
+
+
+def dbnet_set_allocator(alloc=None, free=None) -> None:
+    """Install Python callables as the library's device allocator:
+    alloc(nbytes, stream) -> device address (int) or 0, free(ptr, nbytes,
+    stream).  With no arguments, cudaMalloc is restored.  Affects handles
+    created afterwards."""
+    if alloc is None:
+        _check(lib().dbnet_set_allocator(None), "dbnet_set_allocator")
+        return
+
+    def _a(nbytes, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), int(stream or 0))) or None
+        except Exception:  # noqa: BLE001  -- reported as DBNET_ENOMEM by the library
+            return None
+
+    def _f(ptr, nbytes, stream, ctx):
+        try:
+            free(int(ptr), int(nbytes), int(stream or 0))
+        except Exception:  # noqa: BLE001
+            pass
+    a = dbnet_allocator_t(dbnet_alloc_fn(_a), dbnet_free_fn(_f), None)
+    _allocators.append(a)
+    _check(lib().dbnet_set_allocator(ctypes.byref(a)), "dbnet_set_allocator")
+
+
+def use_torch_allocator(device=None) -> None:
+    """Back every device allocation of later handles with PyTorch's caching
+    allocator (torch.cuda.caching_allocator_alloc / _delete) on `device`
+    (default: the current device), each on the stream of its handle."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device=dev, stream=stream)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+    dbnet_set_allocator(alloc, free)
 
 
 # ------------------------------------------------------------ structures ----
