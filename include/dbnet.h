@@ -196,9 +196,9 @@ typedef struct {
   int64_t step;              /* steps completed */
   int64_t spikes;            /* spikes emitted */
   int64_t events;            /* synaptic events: the out-degree of every spike
-                                handed on, counted as it is emitted, by the
-                                engine behind the handle (for an ensemble member:
-                                the whole ensemble) */
+                                handed on so far (whichever later step adds each
+                                edge), by the engine behind the handle (for an
+                                ensemble member: the whole ensemble) */
   int64_t raster_len;        /* spikes recorded */
   int64_t raster_dropped;    /* spikes not recorded for lack of capacity */
   int64_t bold_samples;      /* BOLD samples recorded */

@@ -451,7 +451,7 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
     hr0.alloc((int64_t)D * seg_cap);
   }
   base.alloc(2);
-  events.alloc(1);
+  events.alloc(2);  // [0] events counted by the deliveries, [1] scratch for the pending ones
   flags.alloc(1);
   CK(cudaMemsetAsync(base.p, 0, sizeof(unsigned long long) * 2, stream));
   CK(cudaMemsetAsync(events.p, 0, sizeof(unsigned long long), stream));
@@ -468,14 +468,14 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev.acc = acc.p;
   dev.stride = stride;
   dev.acc_slots = slots;
-  // V, J, ref, the step's accumulators (and the OU current) held in the L2
-  // across steps when together they take at most half of it
   {
     int dev_id = 0, l2 = 0;
     CK(cudaGetDevice(&dev_id));
     CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev_id));
-    const double state_b = (double)stride * (4.0 + 16.0 + 1.0 + (four ? 16.0 : 8.0) + (any_ext ? 8.0 : 0.0));
-    dev.state_resident = state_b <= 0.5 * (double)l2 ? 1 : 0;
+    // one accumulator slot larger than a quarter of the L2: deliver in
+    // rank phases, each touching about an eighth of the regions at a time
+    const double slot_b = (double)stride * (four ? 16.0 : 8.0);
+    dev.phases = slot_b > 0.25 * (double)l2 ? 8 : 1;
   }
   dev.d_emit = emit_from > 0 ? emit_from : D + 1;
   dev.slot_emit = slots > 1 ? slot_emit.p : nullptr;
@@ -1164,8 +1164,15 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     Engine& e = *h->eng;
     const InstHost& ih = e.inst[h->inst];
     InstDyn d = e.read_dyn(h->inst);
-    unsigned long long ev = 0;
-    CK(cudaMemcpy(&ev, e.events.p, sizeof(ev), cudaMemcpyDeviceToHost));
+    // the deliveries count a spike's events at its delay-1 item; those of
+    // the spikes handed on at the last step are added here
+    CK(cudaMemsetAsync(e.events.p + 1, 0, sizeof(unsigned long long), e.stream));
+    launch_pending_events(e.dev, e.g_host, e.events.p + 1, e.stream);
+    CK(cudaGetLastError());
+    unsigned long long evs[2] = {0, 0};
+    CK(cudaMemcpyAsync(evs, e.events.p, sizeof(evs), cudaMemcpyDeviceToHost, e.stream));
+    CK(cudaStreamSynchronize(e.stream));
+    const unsigned long long ev = evs[0] + evs[1];
     std::memset(out, 0, sizeof(*out));
     out->step = (int64_t)(e.g_host - ih.desc.g0);
     out->spikes = (int64_t)d.spikes;

@@ -197,7 +197,7 @@ struct EngineDev {
   int32_t D;
   int32_t n_inst, n_tiles, total_R;
   int32_t any_ext;       // launch the update variant with the kExt* terms
-  int32_t state_resident;  // the neuron state fits the L2: keep it there between steps
+  int32_t phases;        // rank phases of the delivery's arrival items (1..8)
   int32_t four;          // four accumulator channels per neuron (acc as int4)
 };
 
@@ -216,6 +216,10 @@ void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int6
                    void* seg, int32_t seg_kind, int32_t* indeg, unsigned* wmax_bits, unsigned* err,
                    cudaStream_t s);
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s);
+// adds to *out the out-degrees of the spikes handed on at steps g - 1 ..
+// g - 1 + bin_lead, which no delivery has counted yet
+void launch_pending_events(const EngineDev& e, unsigned long long g, unsigned long long* out,
+                           cudaStream_t s);
 
 enum : unsigned {
   kErrTarget = 1u,

@@ -68,6 +68,7 @@ __device__ __forceinline__ int find_region(const int32_t* __restrict__ ro, int R
 #endif
 constexpr int kWalkU = DBNET_WALK_CHUNKS;
 constexpr int kSegGroup = 32;  // spikes per transposition group of the segment-ring copy
+constexpr int kMaxPhases = 8;  // rank phases of the arrival items (see k_deliver)
 
 __device__ __forceinline__ unsigned long long l2_policy_first() {
   unsigned long long p = 0;
@@ -118,59 +119,6 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* a, unsigned long
 #else
   (void)pol;
   atomicAdd(a, v);
-#endif
-}
-
-// Neuron state: streamed once per step (evict-first) when it is larger than
-// the L2, kept (evict-last) when the whole state fits beside the delivery's
-// working set, so that consecutive steps find it in the L2.
-__device__ __forceinline__ unsigned long long l2_policy_state(int resident) {
-  unsigned long long p = 0;
-#if DBNET_L2_HINTS
-  if (resident) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  else asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-#else
-  (void)resident;
-#endif
-  return p;
-}
-__device__ __forceinline__ float4 ld_state_f4(const float* a, unsigned long long pol) {
-#if DBNET_L2_HINTS
-  float4 v;
-  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
-  return v;
-#else
-  (void)pol;
-  return __ldcs(reinterpret_cast<const float4*>(a));
-#endif
-}
-__device__ __forceinline__ uint32_t ld_state_u32(const void* a, unsigned long long pol) {
-#if DBNET_L2_HINTS
-  uint32_t v;
-  asm("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
-  return v;
-#else
-  (void)pol;
-  return __ldcs(reinterpret_cast<const unsigned int*>(a));
-#endif
-}
-__device__ __forceinline__ void st_state_f4(float* a, float4 v, unsigned long long pol) {
-#if DBNET_L2_HINTS
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x),
-               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
-               : "memory");
-#else
-  (void)pol;
-  __stcs(reinterpret_cast<float4*>(a), v);
-#endif
-}
-__device__ __forceinline__ void st_state_u32(void* a, uint32_t v, unsigned long long pol) {
-#if DBNET_L2_HINTS
-  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
-#else
-  (void)pol;
-  __stcs(reinterpret_cast<unsigned int*>(a), v);
 #endif
 }
 
@@ -291,17 +239,14 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   const int64_t gi0 = (int64_t)tile * kTile + threadIdx.x * 4;
   // (state is streamed once per step: evict-first, so that the delivery's
   // working set keeps the L2)
-  const unsigned long long pol_state = l2_policy_state(e.state_resident);
-  const float4 V4 = ld_state_f4(e.V + gi0, pol_state);
+  const float4 V4 = __ldcs(reinterpret_cast<const float4*>(e.V + gi0));
   float4 J4[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) J4[u] = ld_state_f4(e.J + u * e.stride + gi0, pol_state);
-  const uint32_t rfw = ld_state_u32(e.ref + gi0, pol_state);
-  const uchar4 rf = make_uchar4((unsigned char)rfw, (unsigned char)(rfw >> 8),
-                                (unsigned char)(rfw >> 16), (unsigned char)(rfw >> 24));
+  for (int u = 0; u < 4; ++u) J4[u] = __ldcs(reinterpret_cast<const float4*>(e.J + u * e.stride + gi0));
+  const uchar4 rf = __ldcs(reinterpret_cast<const uchar4*>(e.ref + gi0));
   float4 B4 = make_float4(0.f, 0.f, 0.f, 0.f), F4 = make_float4(1.f, 1.f, 1.f, 1.f);
   if (EXT) {
-    B4 = ld_state_f4(e.Ibg + gi0, pol_state);
+    B4 = __ldcs(reinterpret_cast<const float4*>(e.Ibg + gi0));
     F4 = __ldg(reinterpret_cast<const float4*>(e.fext + gi0));
   }
   // this step's arrivals, per channel (AMPA, NMDA, GABA_A, GABA_B) of the
@@ -434,17 +379,16 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
         v[k] = vn;
       }
     }
-    st_state_f4(e.V + gi0, make_float4(v[0], v[1], v[2], v[3]), pol_state);
+    __stcs(reinterpret_cast<float4*>(e.V + gi0), make_float4(v[0], v[1], v[2], v[3]));
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      st_state_f4(e.J + u * e.stride + gi0, make_float4(j[u][0], j[u][1], j[u][2], j[u][3]),
-                  pol_state);
-    st_state_u32(e.ref + gi0,
-                 (uint32_t)rr[0] | ((uint32_t)rr[1] << 8) | ((uint32_t)rr[2] << 16) |
-                     ((uint32_t)rr[3] << 24),
-                 pol_state);
+      __stcs(reinterpret_cast<float4*>(e.J + u * e.stride + gi0),
+             make_float4(j[u][0], j[u][1], j[u][2], j[u][3]));
+    __stcs(reinterpret_cast<uchar4*>(e.ref + gi0),
+           make_uchar4((unsigned char)rr[0], (unsigned char)rr[1], (unsigned char)rr[2],
+                       (unsigned char)rr[3]));
     if (EXT && (d.ext & kExtOU))
-      st_state_f4(e.Ibg + gi0, make_float4(ib[0], ib[1], ib[2], ib[3]), pol_state);
+      __stcs(reinterpret_cast<float4*>(e.Ibg + gi0), make_float4(ib[0], ib[1], ib[2], ib[3]));
   }
 
   // ---- spikes: one ring append, spike and raster count per block ---------
@@ -475,7 +419,6 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
     s_rbase = d.raster_cap > 0 ? atomicAdd(&e.dyn[inst].raster_count, (unsigned long long)tot) : 0ull;
   }
   __syncthreads();
-  unsigned long long ev = 0;
   if (spk) {
     uint64_t pos = (uint64_t)s_hbase + s_wtot[warp] + (uint32_t)(ps - nsp);
     unsigned long long rpos = s_rbase + s_wtot[warp] + (unsigned long long)(ps - nsp);
@@ -489,9 +432,6 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
         atomicOr(e.flags, kFlagHistOverflow);
       ++pos;
       atomicAdd(&e.cnt[d.rbase + reg[k]], 1);
-      // the spike's synaptic events: its out-degree (Supp. Alg. 2 pushes
-      // every out-edge once), counted as the spike is emitted
-      ev += (unsigned long long)(__ldg(d.row_ptr + li0 + k + 1) - __ldg(d.row_ptr + li0 + k));
       if (d.raster_cap > 0) {
         if (rpos < (unsigned long long)d.raster_cap) {
           d.raster_step[rpos] = (int32_t)n;
@@ -501,9 +441,6 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
       }
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
-  if (lane == 0 && ev) atomicAdd(e.events, ev);
 }
 
 __device__ __forceinline__ uint32_t edge_delay(const uint32_t* col, const uint8_t* dl, int shift,
@@ -542,9 +479,13 @@ struct ItemLoads {
 // the first.
 template <bool FOUR, bool SINGLE>
 __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef sr) {
-  __shared__ unsigned long long s_pre[256];  // items whose delay is below index + 1
-  __shared__ unsigned long long s_wsum[kDelThreads / 32];
-  __shared__ unsigned long long s_total;
+  // arrival items of phase q and delay bucket i start at s_phase[q] +
+  // s_pre[q][i]; bucket i holds ranks [q c/Q, (q+1) c/Q) of the c spikes
+  // handed on at g - i - 1
+  __shared__ unsigned long long s_pre[kMaxPhases][256];
+  __shared__ unsigned long long s_wsum[kMaxPhases][kDelThreads / 32];
+  __shared__ unsigned long long s_phase[kMaxPhases + 1];
+  __shared__ uint32_t s_cnt[256];
   __shared__ __align__(16) uint16_t s_tab[256 * kSegGroup];  // [delay][spike] of a copy group
   __shared__ const uint4* s_row[kSegGroup];
   __shared__ int32_t s_nq[kSegGroup];
@@ -575,7 +516,8 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
     if (c1 > (unsigned long long)e.hist_cap) c1 = (unsigned long long)e.hist_cap;
     if (c1 > (unsigned long long)e.seg_cap) c1 = (unsigned long long)e.seg_cap;
     const unsigned long long want = (c1 + kSegGroup - 1) / kSegGroup;
-    const int most = gridDim.x >= 16 ? (int)gridDim.x / 8 : 1;  // the host launches >= 2 blocks
+    // at most a 32nd of the grid: the copy overlaps the item blocks' work
+    const int most = gridDim.x >= 64 ? (int)gridDim.x / 32 : 1;  // the host launches >= 2 blocks
     nA = want < (unsigned long long)most ? (int)want : most;
   }
   if ((int)blockIdx.x < nA) {
@@ -652,30 +594,50 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
       c = h < (unsigned long long)e.hist_cap ? h : (unsigned long long)e.hist_cap;
     }
   }
-  unsigned long long incl = c;
+  // Phases: the update appends each step's spikes roughly in tile order, so
+  // a spike's rank in its slot follows its region.  Taking the items rank
+  // phase by rank phase (phase q: ranks [q c/Q, (q+1) c/Q) of every delay's
+  // slot) keeps the warps in flight on a narrow band of regions, so the
+  // within-region edges (most of them) add into a slice of the accumulators
+  // that stays in the L2 even when all of them do not fit (Q = 1 when they
+  // do).
+  const int Q = e.phases;
+  s_cnt[threadIdx.x] = (uint32_t)c;
+  unsigned long long incl[kMaxPhases], own[kMaxPhases];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += t;
+  for (int q = 0; q < kMaxPhases; ++q) {
+    own[q] = q < Q ? (q + 1ull) * c / (unsigned long long)Q - q * c / (unsigned long long)Q : 0ull;
+    incl[q] = own[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long t = __shfl_up_sync(kFull, incl[q], o);
+      if (lane >= o) incl[q] += t;
+    }
+    if (lane == 31) s_wsum[q][warp] = incl[q];
   }
-  if (lane == 31) s_wsum[warp] = incl;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < kMaxPhases) {  // warp offsets within each phase
     unsigned long long acc = 0;
     for (int w = 0; w < kDelThreads / 32; ++w) {
-      const unsigned long long t = s_wsum[w];
-      s_wsum[w] = acc;
+      const unsigned long long t = s_wsum[threadIdx.x][w];
+      s_wsum[threadIdx.x][w] = acc;
       acc += t;
     }
-    s_total = acc;
+    s_phase[threadIdx.x + 1] = acc;  // the phase's total, summed below
   }
   __syncthreads();
-  s_pre[threadIdx.x] = s_wsum[warp] + incl - c;
+  if (threadIdx.x == 0) {
+    s_phase[0] = 0ull;
+    for (int q = 0; q < kMaxPhases; ++q) s_phase[q + 1] += s_phase[q];
+  }
+#pragma unroll
+  for (int q = 0; q < kMaxPhases; ++q) s_pre[q][threadIdx.x] = s_wsum[q][warp] + incl[q] - own[q];
+  __syncthreads();
   const int nd = dlim < kDelThreads ? dlim : kDelThreads;  // delay buckets d = 1..nd
   // the emission range: every spike handed on at g - 1 times its delays
   // d_emit..dlim, spike-major so that consecutive lanes take consecutive
   // delays of one row (its segments lie end to end)
-  const unsigned long long W_arr = s_total;
+  const unsigned long long W_arr = s_phase[Q];
   const int ne = e.d_emit <= dlim ? dlim - e.d_emit + 1 : 0;
   unsigned long long c1e = 0;
   if (ne > 0 && g >= 1ull) {
@@ -705,13 +667,17 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
       return;
     }
     p.aslot = aslot_now;
+    int q = 0;  // the phase: the largest q < Q with s_phase[q] <= t
+    for (int step = kMaxPhases / 2; step > 0; step >>= 1)
+      if (q + step < Q && s_phase[q + step] <= t) q += step;
+    const unsigned long long tq = t - s_phase[q];
     int lo = 0, hi = nd - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (s_pre[mid] <= t) lo = mid; else hi = mid - 1;
+      if (s_pre[q][mid] <= tq) lo = mid; else hi = mid - 1;
     }
     p.d = (uint32_t)lo + 1u;
-    p.k = (uint32_t)(t - s_pre[lo]);
+    p.k = (uint32_t)((unsigned long long)q * s_cnt[lo] / (unsigned long long)Q + (tq - s_pre[q][lo]));
     p.slot = (uint32_t)((g - p.d) % (unsigned long long)D);
     p.ent = __ldg(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
     if (p.d >= 2u && p.k < cap) {  // from the delay-major ring (coalesced across lanes)
@@ -724,6 +690,12 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
   };
   // stage two: the item's edge segment [e0, e0 + nseg) from the stage-one
   // loads, or by the graph's own tables when the ring does not hold it
+  // The synaptic events of a spike (its out-degree: Supp. Alg. 2 pushes
+  // every out-edge once) are counted at its delay-1 item, which every spike
+  // handed on has exactly once (arrival, or emission when every delay goes
+  // at emission); the spikes handed on at the last step, not yet reached by
+  // a delivery, are added when the counters are read (k_pending_events).
+  unsigned long long ev = 0;
   auto stage_two = [&](const ItemLoads& p, int64_t& e0, uint32_t& nseg, int& inst, uint32_t& cls) {
     e0 = 0;
     nseg = 0u;
@@ -742,8 +714,9 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
     }
     const InstDesc& dd = e.insts[inst];
     const uint32_t d = p.d;
-    if ((int32_t)d > dd.dmax) return;
     const int64_t j = gidx - dd.base;
+    if (d == 1u) ev += (unsigned long long)(__ldg(dd.row_ptr + j + 1) - __ldg(dd.row_ptr + j));
+    if ((int32_t)d > dd.dmax) return;
     int64_t r0, a, b;
     if (dd.seg_kind == kSeg16 && p.ring) {
       r0 = p.r0;
@@ -857,6 +830,9 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
       }
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
+  if (lane == 0 && ev) atomicAdd(e.events, ev);
 }
 
 // BF16 bit pattern of staged weight e (float32 rounded to nearest even, or
@@ -947,6 +923,30 @@ __global__ void k_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base,
   }
 }
 
+// Out-degree sum of the spikes handed on at steps [r0, r1] (the ones no
+// delivery has reached yet when the counters are read), into *out.
+__global__ void k_pending_events(EngineDev e, long long r0, long long r1, unsigned long long* out) {
+  unsigned long long ev = 0;
+  for (long long r = r0 < 0 ? 0 : r0; r <= r1; ++r) {
+    const unsigned long long slot = (unsigned long long)r % (unsigned long long)e.D;
+    unsigned long long c = e.hcount[slot];
+    if (c > (unsigned long long)e.hist_cap) c = (unsigned long long)e.hist_cap;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < c;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+      const uint32_t ent = e.hist[slot * (unsigned long long)e.hist_cap + k];
+      const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
+      const int inst = e.n_inst == 1 ? 0 : e.tile_info[gidx / kTile].x;
+      if (inst < 0) continue;
+      const InstDesc& dd = e.insts[inst];
+      const int64_t j = gidx - dd.base;
+      ev += (unsigned long long)(dd.row_ptr[j + 1] - dd.row_ptr[j]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
+  if ((threadIdx.x & 31) == 0 && ev) atomicAdd(out, ev);
+}
+
 __global__ void k_max_reduce(const int32_t* __restrict__ a, int64_t n, unsigned* out) {
   unsigned m = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -1019,6 +1019,13 @@ void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int6
   k_ingest<<<(int)blocks, 256, 0, s>>>(N, j0, j1, e_base, row_ptr, col_in, w_in, w2_in, w_dtype,
                                        delay_in, rec, dmax, seg_stride, seg, seg_kind, indeg,
                                        wmax_bits, err);
+}
+
+void launch_pending_events(const EngineDev& e, unsigned long long g, unsigned long long* out,
+                           cudaStream_t s) {
+  if (g == 0) return;
+  const long long r0 = (long long)g - 1, r1 = (long long)g - 1 + e.bin_lead;
+  k_pending_events<<<152, 256, 0, s>>>(e, r0, r1, out);
 }
 
 void launch_max_reduce(const int32_t* a, int64_t n, unsigned* out, cudaStream_t s) {

@@ -306,6 +306,7 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
     e.acc = reinterpret_cast<int2*>(at(kOffAcc));
     e.stride = n_pad;
     e.acc_slots = 1;
+    e.phases = 1;
     e.d_emit = dmax + 2;  // every delay at arrival time
     e.slot_emit = nullptr;
     e.insts = reinterpret_cast<const InstDesc*>(at(kOffDesc));
@@ -334,6 +335,8 @@ extern "C" int dbnet_run_noalloc(const dbnet_device_graph_t* graph,
       launch_update(e, sr, s);
     }
     launch_close(e, (unsigned long long)n_steps, s);
+    // the last step's spikes: their events, not yet reached by a delivery
+    launch_pending_events(e, (unsigned long long)n_steps, e.events, s);
     CK(cudaGetLastError());
     InstDyn out_dyn;
     unsigned long long ev = 0;

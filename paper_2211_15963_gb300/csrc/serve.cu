@@ -355,7 +355,7 @@ void fill_stats(dbsrv* s, dbsrv_stats_t* out) {
   CK(cudaMemcpyAsync(&ev, e.events.p, sizeof(ev), cudaMemcpyDeviceToHost, s->up));
   CK(cudaStreamSynchronize(s->up));
   out->iterations = (int64_t)s->g_done;
-  out->events = (int64_t)ev;
+  out->events = (int64_t)ev;  // counted at each spike's delay-1 delivery
   for (const auto& sl : s->slots) {
     if (sl.req < 0) continue;
     if (sl.cooling) ++out->cooling;
