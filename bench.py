@@ -474,9 +474,12 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(args, dims)
 
+    # host graphs beyond 32 GB stay in pageable memory (pinning most of the
+    # host's memory is not attempted)
+    big_host = dims[0] * dims[1] * args.k_in * (9 if args.two_weights else 7) > 32e9
     res = run_network(args, dims, stream, dev, world, rank, rank_seed(rank, large), args.steps,
                       args.warmup, args.e2e_steps, args.profile_steps,
-                      pageable=args.pageable or large)
+                      pageable=args.pageable or big_host)
     if rank == 0:
         line = {
             "metric": METRIC, "value": res.pop("value"), "unit": UNIT, "n_gpus": world,

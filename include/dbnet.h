@@ -48,6 +48,10 @@ extern "C" {
 #define DBNET_WEIGHT_F32 0
 #define DBNET_WEIGHT_BF16 1
 
+#define DBNET_SCHEDULE_AUTO 0
+#define DBNET_SCHEDULE_SEQUENTIAL 1
+#define DBNET_SCHEDULE_PIPELINED 2
+
 typedef struct dbnet dbnet_t;
 typedef struct dbens dbens_t;
 
@@ -145,9 +149,9 @@ typedef struct {
  *                    automatic emit_delay candidate, first D + 64 steps
  *                    without and D + 64 with it, the last 64 of each timed,
  *                    the faster kept; then 16 x C steps launch the delivery
- *                    kernel with each of C candidate grids (1..4 blocks per
- *                    SM) in turn, timed by CUDA events, and the fastest is
- *                    kept.  Results do not depend on either choice (integer
+ *                    kernel with each of C candidate grids (an eighth, a
+ *                    quarter and half of the SMs, and 1..4 blocks per SM) in
+ *                    turn, timed by CUDA events, and the fastest is kept.  Results do not depend on either choice (integer
  *                    accumulation).  Default 2000 (200 ms at dt 0.1 ms, past
  *                    the onset).
  *   bin_spikes       1: spikes are handed on at bin edges (Supplementary Sec. 3,
@@ -178,7 +182,16 @@ typedef struct {
  *                    On the benchmark networks (in-degree 1,000, 1.3 edges
  *                    per cross-region delay) emission measured slower: its
  *                    scattered additions land in a ring far larger than the
- *                    L2. */
+ *                    L2.
+ *   schedule         how a step's two kernels are ordered (the results are
+ *                    the same): DBNET_SCHEDULE_SEQUENTIAL, the delivery of
+ *                    step n then its update; DBNET_SCHEDULE_PIPELINED, the
+ *                    delivery of step n + 1's delays >= 2 (which need only
+ *                    spikes of steps <= n - 1) on a second stream beside the
+ *                    update of step n, so that the latency-bound delivery
+ *                    runs under the bandwidth-bound update, then the rest of
+ *                    step n + 1's delivery; DBNET_SCHEDULE_AUTO (default):
+ *                    sequential until the autotuner times both. */
 typedef struct {
   double dt_ms, bin_ms, tr_ms, z_scale;
   double bw_kappa, bw_gamma, bw_tau, bw_alpha, bw_rho, bw_V0;
@@ -190,6 +203,8 @@ typedef struct {
   int64_t autotune_at;
   int32_t bin_spikes;
   int32_t emit_delay;
+  int32_t schedule;
+  int32_t reserved_opt;
 } dbnet_options_t;
 
 typedef struct {
@@ -216,7 +231,7 @@ typedef struct {
                                 (and graphs with u32 segment tables) are resolved
                                 from the graph's own tables */
   int32_t emit_delay;        /* delays >= this are added at emission (0: none) */
-  int32_t reserved;
+  int32_t pipelined;         /* 1: the pipelined schedule is in use */
 } dbnet_stats_t;
 
 /* Name of a status code (static string). */

@@ -310,6 +310,8 @@ void check_options(const dbnet_options_t& o) {
   if (o.autotune_at < -1) raise(DBNET_EINVAL, "autotune_at must be -1 or a step index");
   if (o.bin_spikes != 0 && o.bin_spikes != 1) raise(DBNET_EINVAL, "bin_spikes must be 0 or 1");
   if (o.emit_delay < -1 || o.emit_delay > 255) raise(DBNET_EINVAL, "emit_delay must be -1..255");
+  if (o.schedule < DBNET_SCHEDULE_AUTO || o.schedule > DBNET_SCHEDULE_PIPELINED)
+    raise(DBNET_EINVAL, "schedule must be one of DBNET_SCHEDULE_*");
 }
 
 // --------------------------------------------------------------- engine ----
@@ -388,7 +390,9 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   // accumulators: one slot, or a ring of D slots when long delays may be
   // handed on at emission (and the ring takes at most a third of the free
   // memory)
-  int32_t slots = 1;
+  // (two slots at least: the pipelined schedule delivers into step g + 1's
+  // slot while the update reads step g's)
+  int32_t slots = 2;
   if (emit_from > 0) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
@@ -397,6 +401,14 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
     else emit_from = 0;
   }
   acc.alloc((four ? 2 : 1) * stride * (int64_t)slots);  // int2 per neuron, or int4 with four channels
+  // the second stream of the pipelined schedule, ahead of the first
+  {
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&stream2, cudaStreamNonBlocking, hi));
+    CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  }
   CK(cudaMemsetAsync(Ibg.p, 0, sizeof(float) * stride, stream));
   CK(cudaMemsetAsync(fext.p, 0, sizeof(float) * stride, stream));  // read only where kExtHet
   CK(cudaMemsetAsync(V.p, 0, sizeof(float) * stride, stream));
@@ -511,13 +523,19 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
     int dev_id = 0, sms = 0;
     CK(cudaGetDevice(&dev_id));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+    // a few blocks for small networks (whose steps are all latency), up to
+    // four blocks per SM for large ones
+    for (int div : {8, 4, 2})
+      if (sms / div >= 2) tune_grid.push_back(sms / div);
     for (int k = 1; k <= 4 && sms * k <= del_grid; ++k) tune_grid.push_back(sms * k);
     tune_at = (unsigned long long)common.autotune_at;
     if (tune_grid.size() > 1) {
-      tune_ms.assign(tune_grid.size(), 0.0);
+      tune_ms.assign(2 * tune_grid.size(), 0.0);  // each grid, sequential and pipelined
       tune_pending = true;
     }
   }
+  fixed_schedule = common.schedule;
+  pipelined = common.schedule == DBNET_SCHEDULE_PIPELINED;
   CK(cudaGetLastError());
 }
 
@@ -669,6 +687,14 @@ Engine::~Engine() {
   if (gexec) cudaGraphExecDestroy(gexec);
   for (auto& ev : emit_ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto& ev : tune_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (stream2) {
+    cudaStreamSynchronize(stream2);
+    cudaStreamDestroy(stream2);
+  }
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
   if (own_stream && stream) {
     cudaStreamSynchronize(stream);
     cudaStreamDestroy(stream);
@@ -684,6 +710,12 @@ void Engine::check() const {
 // kChunk steps in two halves: the first half finds its iteration at
 // base[0] + i and its last update writes base[1]; the second half reads
 // base[1] and its last update writes base[0] for the next replay.
+// kChunk steps.  Sequential: delivery then update, per step.  Pipelined:
+// the short part of step g's delivery, then step g's update beside the long
+// part of step g + 1's delivery (a fork onto the second stream and a join),
+// so that the latency-bound delivery runs under the bandwidth-bound update;
+// the replay assumes the long part of its first step is already enqueued
+// and leaves the one of the step after its last enqueued.
 void Engine::capture() {
   cudaGraph_t g = nullptr;
   constexpr int half = kChunk / 2;
@@ -692,8 +724,19 @@ void Engine::capture() {
     const int h = i / half, off = i % half;
     const StepRef rd{base.p + h, (unsigned long long)off, nullptr};
     const StepRef ru{base.p + h, (unsigned long long)off, off == half - 1 ? base.p + (1 - h) : nullptr};
-    launch_deliver(dev, del_grid, rd, stream);
+    if (!pipelined) {
+      launch_deliver(dev, del_grid, rd, stream);
+      launch_update(dev, ru, stream);
+      continue;
+    }
+    const StepRef rn{base.p + h, (unsigned long long)off + 1ull, nullptr};  // step g + 1
+    launch_deliver(dev, del_grid, rd, stream, kPartShort);
+    CK(cudaEventRecord(ev_fork, stream));
+    CK(cudaStreamWaitEvent(stream2, ev_fork, 0));
+    launch_deliver(dev, del_grid, rn, stream2, kPartLong);
     launch_update(dev, ru, stream);
+    CK(cudaEventRecord(ev_join, stream2));
+    CK(cudaStreamWaitEvent(stream, ev_join, 0));
   }
   cudaError_t e1 = cudaStreamEndCapture(stream, &g);
   if (e1 != cudaSuccess) raise(DBNET_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
@@ -766,68 +809,100 @@ int64_t Engine::tune_emit(int64_t n) {
   return k;
 }
 
-// Up to n steps of the autotuner: step i of the tuning run launches its
-// delivery with candidate i mod C between two events.  Returns the steps run.
+// Up to n steps of the launch-shape tuner: each candidate -- a delivery grid
+// and the sequential or the pipelined schedule -- runs one captured chunk of
+// kChunk steps between two events (captured beforehand, so the timing is
+// the device's); the fastest stays.  Fewer than kChunk steps run plainly and
+// the tuning goes on at the next call.  Returns the steps run.
 int64_t Engine::tune_steps(int64_t n) {
-  const int C = (int)tune_grid.size();
-  const int total = C * kTuneRounds;
-  const int b = (int)std::min<int64_t>(n, total - tune_done);
-  std::vector<cudaEvent_t> ev(2 * (size_t)b, nullptr);
-  for (auto& x : ev) CK(cudaEventCreate(&x));
-  try {
-    for (int i = 0; i < b; ++i, ++g_host) {
-      const StepRef sr{nullptr, g_host, nullptr};
-      CK(cudaEventRecord(ev[2 * i], stream));
-      launch_deliver(dev, tune_grid[(size_t)((tune_done + i) % C)], sr, stream);
-      CK(cudaEventRecord(ev[2 * i + 1], stream));
-      launch_update(dev, sr, stream);
-    }
-    CK(cudaGetLastError());
-    CK(cudaEventSynchronize(ev[2 * (size_t)b - 1]));
-    for (int i = 0; i < b; ++i) {
-      float ms = 0.0f;
-      CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
-      tune_ms[(size_t)((tune_done + i) % C)] += ms;
-    }
-  } catch (...) {
-    for (auto& x : ev) cudaEventDestroy(x);
-    throw;
+  const int C = (int)tune_grid.size() * 2;
+  if (n < kChunk) {
+    for (int64_t i = 0; i < n; ++i) direct_step();
+    return n;
   }
-  for (auto& x : ev) cudaEventDestroy(x);
-  tune_done += b;
-  if (tune_done == total) {
+  if (fixed_schedule != DBNET_SCHEDULE_AUTO && (tune_done % 2 == 1) != (fixed_schedule == DBNET_SCHEDULE_PIPELINED)) {
+    tune_ms[(size_t)tune_done] = 1e30;  // the other schedule is not a candidate
+    if (++tune_done == C) {
+      int best = 0;
+      for (int c = 1; c < C; ++c)
+        if (tune_ms[(size_t)c] < tune_ms[(size_t)best]) best = c;
+      set_shape(tune_grid[(size_t)(best / 2)], best % 2 == 1);
+      tune_pending = false;
+    }
+    return 0;
+  }
+  set_shape(tune_grid[(size_t)(tune_done / 2)], tune_done % 2 == 1);
+  if (!pipelined && long_pending) {
+    direct_step();
+    return 1;
+  }
+  if (!gexec) capture();
+  if (pipelined && !long_pending) {
+    launch_deliver(dev, del_grid, StepRef{nullptr, g_host, nullptr}, stream, kPartLong);
+    long_pending = true;
+  }
+  if (!tune_ev[0]) {
+    CK(cudaEventCreate(&tune_ev[0]));
+    CK(cudaEventCreate(&tune_ev[1]));
+  }
+  CK(cudaEventRecord(tune_ev[0], stream));
+  run_plain(kChunk);
+  CK(cudaEventRecord(tune_ev[1], stream));
+  CK(cudaEventSynchronize(tune_ev[1]));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, tune_ev[0], tune_ev[1]));
+  tune_ms[(size_t)tune_done] = ms;
+  if (++tune_done == C) {
     int best = 0;
     for (int c = 1; c < C; ++c)
       if (tune_ms[(size_t)c] < tune_ms[(size_t)best]) best = c;
-    if (tune_grid[(size_t)best] != del_grid) {
-      del_grid = tune_grid[(size_t)best];
-      if (gexec) {
-        CK(cudaGraphExecDestroy(gexec));
-        gexec = nullptr;
-      }
-    }
+    set_shape(tune_grid[(size_t)(best / 2)], best % 2 == 1);
     tune_pending = false;
   }
-  return b;
+  return kChunk;
+}
+
+void Engine::set_shape(int grid, bool pip) {
+  if (grid == del_grid && pip == pipelined) return;
+  del_grid = grid;
+  pipelined = pip;
+  if (gexec) {
+    CK(cudaStreamSynchronize(stream));
+    CK(cudaGraphExecDestroy(gexec));
+    gexec = nullptr;
+  }
 }
 
 // n steps with the current delivery grid: whole chunks from the captured
 // graph, the rest as direct launches
 void Engine::run_plain(int64_t n) {
+  if (n >= kChunk && !pipelined && long_pending) {  // the pending long part first
+    direct_step();
+    --n;
+  }
   if (n >= kChunk) {
     if (!gexec) capture();
+    if (pipelined && !long_pending)
+      launch_deliver(dev, del_grid, StepRef{nullptr, g_host, nullptr}, stream, kPartLong);
     launch_set_base(base.p, g_host, stream);
     while (n >= kChunk) {
       CK(cudaGraphLaunch(gexec, stream));
       n -= kChunk;
       g_host += kChunk;
     }
+    long_pending = pipelined;
   }
-  for (; n > 0; --n, ++g_host) {
-    const StepRef sr{nullptr, g_host, nullptr};
-    launch_deliver(dev, del_grid, sr, stream);
-    launch_update(dev, sr, stream);
-  }
+  for (; n > 0; --n) direct_step();
+}
+
+// One step by direct launches: the delivery (only its short part when the
+// long part is already enqueued), then the update.
+void Engine::direct_step() {
+  const StepRef sr{nullptr, g_host, nullptr};
+  launch_deliver(dev, del_grid, sr, stream, long_pending ? kPartShort : kPartAll);
+  launch_update(dev, sr, stream);
+  long_pending = false;
+  ++g_host;
 }
 
 void Engine::step_timed(int64_t n, double* ms) {
@@ -843,7 +918,8 @@ void Engine::step_timed(int64_t n, double* ms) {
       for (int i = 0; i < b; ++i, ++g_host) {
         const StepRef sr{nullptr, g_host, nullptr};
         CK(cudaEventRecord(ev[3 * i], stream));
-        launch_deliver(dev, del_grid, sr, stream);
+        launch_deliver(dev, del_grid, sr, stream, long_pending ? kPartShort : kPartAll);
+        long_pending = false;
         CK(cudaEventRecord(ev[3 * i + 1], stream));
         launch_update(dev, sr, stream);
         CK(cudaEventRecord(ev[3 * i + 2], stream));
@@ -1188,6 +1264,7 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     out->deliver_blocks = e.del_grid;
     out->seg_ring = ih.graph->seg_kind == kSeg16 ? (int32_t)e.dev.seg_cap : 0;
     out->emit_delay = e.dev.d_emit <= e.dev.D ? e.dev.d_emit : 0;
+    out->pipelined = e.pipelined ? 1 : 0;
     out->autotuned = (!e.tune_pending && !e.tune_grid.empty()) ? 1 : 0;
     out->two_weights = e.dev.four;
   });

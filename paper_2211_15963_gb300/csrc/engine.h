@@ -205,7 +205,8 @@ struct EngineDev {
 void launch_init_state(const EngineDev& e, int inst, int n_tiles_inst, int first_tile,
                        cudaStream_t s);
 void launch_update(const EngineDev& e, StepRef sr, cudaStream_t s);
-void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s);
+enum : int { kPartAll = 0, kPartLong = 1, kPartShort = 2 };  // see k_deliver
+void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s, int part = kPartAll);
 // closes the bin that ends with iteration g - 1 (if any) for every region
 void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s);
 void launch_set_base(unsigned long long* base, unsigned long long g, cudaStream_t s);

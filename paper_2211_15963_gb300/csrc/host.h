@@ -249,15 +249,25 @@ struct Engine {
   EngineDev dev{};
   cudaGraphExec_t gexec = nullptr;
   int del_grid = 0;
-  // delivery-grid autotuner: from iteration tune_at on, kTuneRounds rounds
-  // over the candidate grids, each step's delivery timed by CUDA events;
-  // the fastest total wins and the step graph is captured again
-  static constexpr int kTuneRounds = 16;
+  // launch-shape autotuner: from iteration tune_at on, one captured chunk
+  // per candidate (delivery grid x sequential or pipelined schedule), timed
+  // by CUDA events; the fastest stays and the step graph is captured again
   bool tune_pending = false;
   unsigned long long tune_at = 0;
   int tune_done = 0;                  // steps timed so far
   std::vector<int> tune_grid;         // candidates
-  std::vector<double> tune_ms;        // summed delivery time per candidate
+  std::vector<double> tune_ms;        // chunk time per candidate (grid-major, schedule)
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  // pipelined schedule: the long part of step g + 1's delivery beside step
+  // g's update on a second stream; long_pending: that part of step g_host is
+  // already enqueued
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool pipelined = false;
+  bool long_pending = false;
+  int32_t fixed_schedule = 0;         // DBNET_SCHEDULE_*
+  void direct_step();
+  void set_shape(int grid, bool pipelined);
   // emission threshold: the engine's current d_emit (D + 1: none) and the
   // candidate the tuner weighs against "none" (0: no ring, nothing to tune).
   // Each candidate runs kEmitWarm + kEmitTimed steps (D of them for the

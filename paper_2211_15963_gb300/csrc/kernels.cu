@@ -477,8 +477,14 @@ struct ItemLoads {
 // never carries into the high one.  SINGLE: the engine holds one instance
 // (a network, or the allocation-free run), so every spike's descriptor is
 // the first.
+// part: kPartAll does the whole delivery of iteration g.  The pipelined
+// schedule splits it: kPartLong, the arrival items of delays >= 2, which
+// read only spikes of steps <= g - 2 and so run beside the update of
+// iteration g - 1; then kPartShort after that update: the bin close, the
+// ring bookkeeping, the segment-ring copy of step g - 1's spikes, the
+// delay-1 items and the emission items.
 template <bool FOUR, bool SINGLE>
-__global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef sr) {
+__global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef sr, int part) {
   // arrival items of phase q and delay bucket i start at s_phase[q] +
   // s_pre[q][i]; bucket i holds ranks [q c/Q, (q+1) c/Q) of the c spikes
   // handed on at g - i - 1
@@ -495,12 +501,14 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   // close the bin that ended with the previous iteration, one region per thread
-  for (int gr = gtid; gr < e.total_R; gr += gridDim.x * blockDim.x) close_region(e, gr, g);
+  const bool do_short = part != kPartLong, do_long = part != kPartShort;
+  if (do_short)
+    for (int gr = gtid; gr < e.total_R; gr += gridDim.x * blockDim.x) close_region(e, gr, g);
   // the slot that the updates from this iteration on fill (a bin later with
   // spike binning) was last read by the previous iteration; the slot handed
   // on at g - 1 gets its long delays now, at emission, when d_emit allows
   const unsigned long long s1 = (g + (unsigned long long)D - 1ull) % (unsigned long long)D;
-  if (gtid == 0) {
+  if (gtid == 0 && do_short) {
     e.hcount[(g + (unsigned long long)e.bin_lead) % (unsigned long long)D] = 0u;
     if (e.slot_emit) e.slot_emit[s1] = (uint16_t)e.d_emit;
   }
@@ -511,7 +519,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
   int nA = 0;
   // delay-major planes the later arrival items read: delays below d_emit
   const int planes = e.dcap < e.d_emit - 1 ? e.dcap : e.d_emit - 1;
-  if (e.seg_cap > 0 && g >= 1ull && planes > 1) {
+  if (e.seg_cap > 0 && g >= 1ull && planes > 1 && do_short) {
     c1 = e.hcount[s1];
     if (c1 > (unsigned long long)e.hist_cap) c1 = (unsigned long long)e.hist_cap;
     if (c1 > (unsigned long long)e.seg_cap) c1 = (unsigned long long)e.seg_cap;
@@ -584,7 +592,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
   const int dlim = D - 1 - e.bin_lead;
   unsigned long long c = 0;
   const int dme = threadIdx.x + 1;
-  if (dme <= dlim && g >= (unsigned long long)dme) {
+  if (dme <= dlim && g >= (unsigned long long)dme && (dme == 1 ? do_short : do_long)) {
     const unsigned long long sl = (g - dme) % (unsigned long long)D;
     // delays at or above the threshold in force when that slot was handed
     // on went out at emission
@@ -640,7 +648,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
   const unsigned long long W_arr = s_phase[Q];
   const int ne = e.d_emit <= dlim ? dlim - e.d_emit + 1 : 0;
   unsigned long long c1e = 0;
-  if (ne > 0 && g >= 1ull) {
+  if (ne > 0 && g >= 1ull && do_short) {
     c1e = e.hcount[s1];
     if (c1e > (unsigned long long)e.hist_cap) c1e = (unsigned long long)e.hist_cap;
   }
@@ -997,14 +1005,14 @@ int deliver_grid() {
   return g_deliver_grid;
 }
 
-void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s) {
+void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s, int part) {
   if (grid < 2) grid = 2;  // with a segment ring, block 0 may take no items
   if (e.n_inst == 1) {
-    if (e.four) k_deliver<true, true><<<grid, kDelThreads, 0, s>>>(e, sr);
-    else k_deliver<false, true><<<grid, kDelThreads, 0, s>>>(e, sr);
+    if (e.four) k_deliver<true, true><<<grid, kDelThreads, 0, s>>>(e, sr, part);
+    else k_deliver<false, true><<<grid, kDelThreads, 0, s>>>(e, sr, part);
   } else {
-    if (e.four) k_deliver<true, false><<<grid, kDelThreads, 0, s>>>(e, sr);
-    else k_deliver<false, false><<<grid, kDelThreads, 0, s>>>(e, sr);
+    if (e.four) k_deliver<true, false><<<grid, kDelThreads, 0, s>>>(e, sr, part);
+    else k_deliver<false, false><<<grid, kDelThreads, 0, s>>>(e, sr, part);
   }
 }
 

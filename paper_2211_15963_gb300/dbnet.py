@@ -31,6 +31,7 @@ DBNET_ERANGE = -7
 DBNET_EUNSUPPORTED = -8
 DBNET_WEIGHT_F32 = 0
 DBNET_WEIGHT_BF16 = 1
+DBNET_SCHEDULE_AUTO, DBNET_SCHEDULE_SEQUENTIAL, DBNET_SCHEDULE_PIPELINED = 0, 1, 2
 DBENS_DIFFUSION = 0
 DBENS_GLOBAL = 1
 
@@ -65,7 +66,7 @@ class dbnet_options_t(ctypes.Structure):
                 ("bw_rho", _d), ("bw_V0", _d), ("seed", _u64), ("net_id", _u64),
                 ("fixed_shift", _i32), ("precision", _i32), ("raster_capacity", _i64),
                 ("bold_capacity", _i64), ("autotune_at", _i64), ("bin_spikes", _i32),
-                ("emit_delay", _i32)]
+                ("emit_delay", _i32), ("schedule", _i32), ("reserved_opt", _i32)]
 
 
 class dbnet_stats_t(ctypes.Structure):
@@ -73,7 +74,7 @@ class dbnet_stats_t(ctypes.Structure):
                 ("raster_dropped", _i64), ("bold_samples", _i64), ("fixed_shift", _i32),
                 ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32),
                 ("deliver_blocks", _i32), ("autotuned", _i32), ("two_weights", _i32),
-                ("seg_ring", _i32), ("emit_delay", _i32), ("reserved", _i32)]
+                ("seg_ring", _i32), ("emit_delay", _i32), ("pipelined", _i32)]
 
 
 class dbnet_device_graph_t(ctypes.Structure):
