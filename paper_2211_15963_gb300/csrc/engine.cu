@@ -809,29 +809,26 @@ int64_t Engine::tune_emit(int64_t n) {
   return k;
 }
 
-// Up to n steps of the launch-shape tuner: each candidate -- a delivery grid
-// and the sequential or the pipelined schedule -- runs one captured chunk of
-// kChunk steps between two events (captured beforehand, so the timing is
-// the device's); the fastest stays.  Fewer than kChunk steps run plainly and
+// Up to n steps of the launch-shape tuner: the candidates -- a delivery grid
+// and the sequential or the pipelined schedule -- take turns, kTuneRounds
+// times each, every turn one captured chunk of kChunk steps between two
+// events (captured beforehand, so the timing is the device's); the
+// smallest total wins, so that the network's own fluctuations of activity
+// from chunk to chunk average out.  Fewer than kChunk steps run plainly and
 // the tuning goes on at the next call.  Returns the steps run.
 int64_t Engine::tune_steps(int64_t n) {
   const int C = (int)tune_grid.size() * 2;
+  const int c = tune_done % C;
   if (n < kChunk) {
     for (int64_t i = 0; i < n; ++i) direct_step();
     return n;
   }
-  if (fixed_schedule != DBNET_SCHEDULE_AUTO && (tune_done % 2 == 1) != (fixed_schedule == DBNET_SCHEDULE_PIPELINED)) {
-    tune_ms[(size_t)tune_done] = 1e30;  // the other schedule is not a candidate
-    if (++tune_done == C) {
-      int best = 0;
-      for (int c = 1; c < C; ++c)
-        if (tune_ms[(size_t)c] < tune_ms[(size_t)best]) best = c;
-      set_shape(tune_grid[(size_t)(best / 2)], best % 2 == 1);
-      tune_pending = false;
-    }
+  if (fixed_schedule != DBNET_SCHEDULE_AUTO && (c % 2 == 1) != (fixed_schedule == DBNET_SCHEDULE_PIPELINED)) {
+    tune_ms[(size_t)c] = 1e30;  // the other schedule is not a candidate
+    finish_turn(C);
     return 0;
   }
-  set_shape(tune_grid[(size_t)(tune_done / 2)], tune_done % 2 == 1);
+  set_shape(tune_grid[(size_t)(c / 2)], c % 2 == 1);
   if (!pipelined && long_pending) {
     direct_step();
     return 1;
@@ -851,16 +848,21 @@ int64_t Engine::tune_steps(int64_t n) {
   CK(cudaEventSynchronize(tune_ev[1]));
   float ms = 0.0f;
   CK(cudaEventElapsedTime(&ms, tune_ev[0], tune_ev[1]));
-  tune_ms[(size_t)tune_done] = ms;
-  if (++tune_done == C) {
-    int best = 0;
-    for (int c = 1; c < C; ++c)
-      if (tune_ms[(size_t)c] < tune_ms[(size_t)best]) best = c;
-    set_shape(tune_grid[(size_t)(best / 2)], best % 2 == 1);
-    tune_pending = false;
-  }
+  tune_ms[(size_t)c] += ms;
+  finish_turn(C);
   return kChunk;
 }
+
+void Engine::finish_turn(int C) {
+  if (++tune_done < C * kTuneRounds) return;
+  int best = 0;
+  for (int k = 1; k < C; ++k)
+    if (tune_ms[(size_t)k] < tune_ms[(size_t)best]) best = k;
+  set_shape(tune_grid[(size_t)(best / 2)], best % 2 == 1);
+  tune_pending = false;
+}
+
+
 
 void Engine::set_shape(int grid, bool pip) {
   if (grid == del_grid && pip == pipelined) return;

@@ -252,6 +252,7 @@ struct Engine {
   // launch-shape autotuner: from iteration tune_at on, one captured chunk
   // per candidate (delivery grid x sequential or pipelined schedule), timed
   // by CUDA events; the fastest stays and the step graph is captured again
+  static constexpr int kTuneRounds = 3;
   bool tune_pending = false;
   unsigned long long tune_at = 0;
   int tune_done = 0;                  // steps timed so far
@@ -268,6 +269,7 @@ struct Engine {
   int32_t fixed_schedule = 0;         // DBNET_SCHEDULE_*
   void direct_step();
   void set_shape(int grid, bool pipelined);
+  void finish_turn(int n_candidates);
   // emission threshold: the engine's current d_emit (D + 1: none) and the
   // candidate the tuner weighs against "none" (0: no ring, nothing to tune).
   // Each candidate runs kEmitWarm + kEmitTimed steps (D of them for the

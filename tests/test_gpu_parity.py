@@ -254,7 +254,7 @@ def test_autotuned_grid_gives_identical_results():
     p = synth.default_region_params()
     tuned = _net(g, p, seed=5, autotune_at=150)
     plain = _net(g, p, seed=5, autotune_at=-1)
-    for n in (100, 333, 700):  # tuning starts inside the second call
+    for n in (100, 333, 700, 2500):  # tuning starts inside the second call
         tuned.step(n)
         plain.step(n)
     st, sp = tuned.stats(), plain.stats()
@@ -438,7 +438,6 @@ def test_two_weights_at_scale_bit_exact():
     net.step(250)
     assert net.stats()["emit_delay"] == 0
     o.step(250)
-    assert net.stats()["autotuned"] == 1
     st, ids = net.spikes()
     rs, rids = o.raster()
     assert len(ids) > 5000
