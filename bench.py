@@ -57,9 +57,17 @@ UNIT = "events/s"
 # (regions, neurons per region) of the two network workloads
 WORKLOAD_DIMS = {"large": (200, 100_000), "mid": (100, 20_000)}
 # kernels launched per dbnet_step(10,000): 156 replays of the 64-step graph
-# (128 launches each) + 16 direct steps (2 each) + the graph's base word + the
-# bin close at the end of the call
+# (128 launches each; 192 on the pipelined schedule, whose steps are three
+# launches, plus the long part launched ahead of the first replay) + 16
+# direct steps (2 each) + the graph's base word + the bin close at the end of
+# the call
 LAUNCHES_PER_BIO_S = 156 * 128 + 16 * 2 + 2
+
+
+def launches_per_call(n_steps, pipelined):
+    chunks, rest = divmod(n_steps, 64)
+    return chunks * (192 if pipelined else 128) + 2 * rest + (2 if chunks else 1) + (
+        1 if pipelined and chunks else 0)
 
 
 def parse():
@@ -74,6 +82,11 @@ def parse_from(argv):
     ap.add_argument("--rate", type=int, default=15, choices=sorted(RATE_DRIVE))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--tune-at", type=int, default=2000,
+                    help="Euler step at which the library tunes the delivery's launch shape")
+    ap.add_argument("--step-ms", type=float, default=1000.0,
+                    help="biological time per benchmark step of the network workloads (ms); "
+                         "shorter steps only for profiling runs")
     ap.add_argument("--profile-steps", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -311,6 +324,7 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
     from paper_2211_15963_gb300 import dbnet
 
     R, S = dims
+    n_step = int(round(getattr(args, "step_ms", 1000.0) / 0.1))  # Euler steps per benchmark step
     alloc, keep = (None, None) if pageable else pinned_alloc(torch)
     t_gen = time.perf_counter()
     g = synth.make_graph([S] * R, args.k_in, seed, k_within=int(round(0.8 * args.k_in)),
@@ -319,14 +333,15 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
         g = synth.with_second_weight(g, seed + 5, alloc=alloc)
     t_gen = time.perf_counter() - t_gen
     params = params_for(args.rate, args.k_in)
-    opts = dict(seed=seed + 1, net_id=rank, bin_spikes=1 if args.bin_spikes else 0)
+    opts = dict(seed=seed + 1, net_id=rank, bin_spikes=1 if args.bin_spikes else 0,
+                autotune_at=getattr(args, "tune_at", 2000))
 
     t_create = time.perf_counter()
     net = dbnet.Network(g, params, opts, stream)
     net.sync()
     t_create = time.perf_counter() - t_create
     for _ in range(warmup):
-        net.step(STEPS_PER_BIO_S)
+        net.step(n_step)
     net.sync()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(timed_steps)]
@@ -343,7 +358,7 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
         with torch.cuda.stream(stream):
             flush.zero_()
         starts[k].record(stream)
-        net.step(STEPS_PER_BIO_S)
+        net.step(n_step)
         ends[k].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -392,8 +407,8 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
                              "graph-replayed step time (%d + %d B per neuron and event)"
                              % (UPDATE_BYTES_PER_NEURON_FOUR if two else UPDATE_BYTES_PER_NEURON,
                                 DELIVER_BYTES_PER_EVENT_TWO if two else DELIVER_BYTES_PER_EVENT),
-                     "achieved": step_bytes / (ms_per_step / STEPS_PER_BIO_S * 1e-3) / 1e9,
-                     "frac": step_bytes / (ms_per_step / STEPS_PER_BIO_S * 1e-3) / 1e9 / hbm}}
+                     "achieved": step_bytes / (ms_per_step / n_step * 1e-3) / 1e9,
+                     "frac": step_bytes / (ms_per_step / n_step * 1e-3) / 1e9 / hbm}}
     stats = net.stats()
     net.close()
     del flush
@@ -431,12 +446,14 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
                "steps": e2e_steps, "bold_samples": int(len(y))}
     out = {
         "value": events_all / (ms_all * 1e-3), "ms_per_step": ms_per_step,
-        "rtf": ms_per_step / 1e3,
-        "neuron_updates_per_s": neurons_all * STEPS_PER_BIO_S * timed_steps / (ms_all * 1e-3),
-        "mean_rate_hz": spikes_all / neurons_all / timed_steps,
+        "rtf": ms_per_step / (n_step * 0.1),
+        "neuron_updates_per_s": neurons_all * n_step * timed_steps / (ms_all * 1e-3),
+        "mean_rate_hz": spikes_all / neurons_all / timed_steps / (n_step * 1e-4),
         "wall_s_timed": wall, "generate_s": t_gen, "create_s": t_create,
         "deliver_blocks": stats["deliver_blocks"], "segment_ring_spikes": stats["seg_ring"],
-        "clocks": clk, "e2e": e2e, "gpu_launches": LAUNCHES_PER_BIO_S * timed_steps,
+        "clocks": clk, "e2e": e2e,
+        "gpu_launches": launches_per_call(n_step, bool(stats["pipelined"])) * timed_steps,
+        "schedule": "pipelined" if stats["pipelined"] else "sequential",
         "roofline": roof,
     }
     del g, keep
@@ -509,6 +526,7 @@ def run_extras(args, stream, dev):
     out["mid"] = {"config": workload_config(mid_args, 1, WORKLOAD_DIMS["mid"])["workload"],
                   "value": m["value"], "unit": UNIT, "rtf": m["rtf"], "steps": 3, "warmup": 1,
                   "mean_rate_hz": m["mean_rate_hz"], "deliver_blocks": m["deliver_blocks"],
+                  "schedule": m["schedule"],
                   "k_update_us": kern["k_update"]["avg_us"], "k_update_frac": kern["k_update"]["frac"],
                   "k_deliver_us": kern["k_deliver"]["avg_us"],
                   "k_deliver_frac": kern["k_deliver"]["frac"],
