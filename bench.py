@@ -60,11 +60,16 @@ WORKLOAD_DIMS = {"large": (200, 100_000), "mid": (100, 20_000)}
 # (128 launches each; 192 on the pipelined schedule, whose steps are three
 # launches, plus the long part launched ahead of the first replay) + 16
 # direct steps (2 each) + the graph's base word + the bin close at the end of
-# the call
+# the call; on the persistent schedule one launch per 4,096 steps + the bin
+# close
 LAUNCHES_PER_BIO_S = 156 * 128 + 16 * 2 + 2
+SCHEDULES = {1: "sequential", 2: "pipelined", 3: "persistent"}
 
 
-def launches_per_call(n_steps, pipelined):
+def launches_per_call(n_steps, schedule):
+    if schedule == "persistent":
+        return -(-n_steps // 4096) + 1
+    pipelined = schedule == "pipelined"
     chunks, rest = divmod(n_steps, 64)
     return chunks * (192 if pipelined else 128) + 2 * rest + (2 if chunks else 1) + (
         1 if pipelined and chunks else 0)
@@ -452,8 +457,8 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
         "wall_s_timed": wall, "generate_s": t_gen, "create_s": t_create,
         "deliver_blocks": stats["deliver_blocks"], "segment_ring_spikes": stats["seg_ring"],
         "clocks": clk, "e2e": e2e,
-        "gpu_launches": launches_per_call(n_step, bool(stats["pipelined"])) * timed_steps,
-        "schedule": "pipelined" if stats["pipelined"] else "sequential",
+        "gpu_launches": launches_per_call(n_step, SCHEDULES[stats["schedule"]]) * timed_steps,
+        "schedule": SCHEDULES[stats["schedule"]],
         "roofline": roof,
     }
     del g, keep

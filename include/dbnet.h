@@ -38,8 +38,9 @@ extern "C" {
 #define DBNET_EINVAL (-1)      /* malformed graph, parameters or arguments */
 #define DBNET_ENOMEM (-2)      /* device or host allocation failed */
 #define DBNET_ECUDA (-3)       /* a CUDA runtime call failed */
-#define DBNET_ETIMEOUT (-4)    /* reserved: no kernel of this library waits on
-                                  the device (each step is two plain launches) */
+#define DBNET_ETIMEOUT (-4)    /* a grid barrier of the persistent stepper
+                                  waited longer than its limit (1 s); the
+                                  handle is then poisoned */
 #define DBNET_EOVERFLOW (-5)   /* fixed-point accumulation could overflow int32 */
 #define DBNET_ESTATE (-6)      /* handle poisoned by an earlier failure */
 #define DBNET_ERANGE (-7)      /* a caller buffer or a fixed capacity is too small */
@@ -51,6 +52,7 @@ extern "C" {
 #define DBNET_SCHEDULE_AUTO 0
 #define DBNET_SCHEDULE_SEQUENTIAL 1
 #define DBNET_SCHEDULE_PIPELINED 2
+#define DBNET_SCHEDULE_PERSISTENT 3
 
 typedef struct dbnet dbnet_t;
 typedef struct dbens dbens_t;
@@ -148,10 +150,12 @@ typedef struct {
  *   autotune_at      step at which the delivery is tuned (-1 = never): with an
  *                    automatic emit_delay candidate, first D + 64 steps
  *                    without and D + 64 with it, the last 64 of each timed,
- *                    the faster kept; then 16 x C steps launch the delivery
- *                    kernel with each of C candidate grids (an eighth, a
- *                    quarter and half of the SMs, and 1..4 blocks per SM) in
- *                    turn, timed by CUDA events, and the fastest is kept.  Results do not depend on either choice (integer
+ *                    the faster kept; then every launch shape -- a delivery
+ *                    grid (an eighth, a quarter and half of the SMs, and 1..4
+ *                    blocks per SM) on each schedule the schedule option
+ *                    admits -- runs 64 steps timed by CUDA events, three
+ *                    times each in turn, and the smallest total is kept.
+ *                    Results depend on none of these choices (integer
  *                    accumulation).  Default 2000 (200 ms at dt 0.1 ms, past
  *                    the onset).
  *   bin_spikes       1: spikes are handed on at bin edges (Supplementary Sec. 3,
@@ -190,8 +194,19 @@ typedef struct {
  *                    spikes of steps <= n - 1) on a second stream beside the
  *                    update of step n, so that the latency-bound delivery
  *                    runs under the bandwidth-bound update, then the rest of
- *                    step n + 1's delivery; DBNET_SCHEDULE_AUTO (default):
- *                    sequential until the autotuner times both. */
+ *                    step n + 1's delivery; DBNET_SCHEDULE_PERSISTENT, many
+ *                    steps in one cooperative launch (the same delivery and
+ *                    update device code, separated by grid barriers whose
+ *                    waits give up after 1 s with DBNET_ETIMEOUT), which
+ *                    saves the two launches per step where a step's kernels
+ *                    are short; DBNET_SCHEDULE_AUTO (default): sequential
+ *                    until the autotuner times all three.
+ *   deliver_blocks   blocks of the delivery grid (>= 2; on the persistent
+ *                    schedule at most the co-resident blocks, else
+ *                    DBNET_EINVAL at the first step), and the autotuner then
+ *                    tunes only the schedule; 0 (default): 1 to 4 blocks
+ *                    per SM, as the occupancy allows, until the autotuner
+ *                    picks one. */
 typedef struct {
   double dt_ms, bin_ms, tr_ms, z_scale;
   double bw_kappa, bw_gamma, bw_tau, bw_alpha, bw_rho, bw_V0;
@@ -204,7 +219,7 @@ typedef struct {
   int32_t bin_spikes;
   int32_t emit_delay;
   int32_t schedule;
-  int32_t reserved_opt;
+  int32_t deliver_blocks;
 } dbnet_options_t;
 
 typedef struct {
@@ -231,7 +246,8 @@ typedef struct {
                                 (and graphs with u32 segment tables) are resolved
                                 from the graph's own tables */
   int32_t emit_delay;        /* delays >= this are added at emission (0: none) */
-  int32_t pipelined;         /* 1: the pipelined schedule is in use */
+  int32_t schedule;          /* DBNET_SCHEDULE_SEQUENTIAL, _PIPELINED or
+                                _PERSISTENT: the schedule in use */
 } dbnet_stats_t;
 
 /* Name of a status code (static string). */
@@ -351,6 +367,18 @@ int dbnet_set_ibg(dbnet_t* h, const float* I_bg);
 int dbnet_stats(dbnet_t* h, dbnet_stats_t* out);
 
 void dbnet_destroy(dbnet_t* h);
+
+/* Checks the grid barrier of the persistent stepper on the current device
+ * (no counterpart in the paper): one cooperative launch of `blocks` blocks
+ * (1 .. the number of SMs) passes `rounds` (>= 1) barriers, each of which
+ * expects `missing` arrivals more than the grid makes.  With missing = 0
+ * every barrier completes and the call returns DBNET_OK; with missing > 0
+ * nothing makes the awaited arrivals, the first wait gives up after
+ * limit_us microseconds (1 .. 10^7) of the device's global timer, every
+ * block returns, and the call returns DBNET_ETIMEOUT with the device still
+ * usable.  The call synchronises the device's default stream.  DBNET_EINVAL
+ * for arguments outside those ranges. */
+int dbnet_barrier_probe(int32_t blocks, int32_t missing, int32_t rounds, int64_t limit_us);
 
 /* ---------------------------------------------------------------------------
  * Ensemble of networks for HMDA (Methods, "Statistical inference ... by

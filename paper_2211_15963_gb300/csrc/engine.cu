@@ -310,8 +310,10 @@ void check_options(const dbnet_options_t& o) {
   if (o.autotune_at < -1) raise(DBNET_EINVAL, "autotune_at must be -1 or a step index");
   if (o.bin_spikes != 0 && o.bin_spikes != 1) raise(DBNET_EINVAL, "bin_spikes must be 0 or 1");
   if (o.emit_delay < -1 || o.emit_delay > 255) raise(DBNET_EINVAL, "emit_delay must be -1..255");
-  if (o.schedule < DBNET_SCHEDULE_AUTO || o.schedule > DBNET_SCHEDULE_PIPELINED)
+  if (o.schedule < DBNET_SCHEDULE_AUTO || o.schedule > DBNET_SCHEDULE_PERSISTENT)
     raise(DBNET_EINVAL, "schedule must be one of DBNET_SCHEDULE_*");
+  if (o.deliver_blocks < 0 || o.deliver_blocks == 1 || o.deliver_blocks > (1 << 20))
+    raise(DBNET_EINVAL, "deliver_blocks must be 0 (automatic) or 2 .. 2^20");
 }
 
 // --------------------------------------------------------------- engine ----
@@ -518,24 +520,39 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
   dev.total_R = 0;
   n_tiles = 0;
   total_R = 0;
-  del_grid = deliver_grid();
+  del_grid = common.deliver_blocks > 0 ? common.deliver_blocks : deliver_grid();
+  pbar.alloc(1);
+  persist_max = persist_max_grid(dev);
+  fixed_schedule = common.schedule;
+  pipelined = common.schedule == DBNET_SCHEDULE_PIPELINED;
+  persistent = common.schedule == DBNET_SCHEDULE_PERSISTENT;
+  if (persistent) {
+    if (persist_max < 2) raise(DBNET_EUNSUPPORTED, "the persistent stepper cannot be made co-resident");
+    if (common.deliver_blocks > persist_max)
+      raise(DBNET_EINVAL, "deliver_blocks exceeds the persistent stepper's co-resident blocks (" +
+                              std::to_string(persist_max) + ")");
+    del_grid = std::min(del_grid, persist_max);
+  }
   if (common.autotune_at >= 0) {
     int dev_id = 0, sms = 0;
     CK(cudaGetDevice(&dev_id));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
-    // a few blocks for small networks (whose steps are all latency), up to
-    // four blocks per SM for large ones
-    for (int div : {8, 4, 2})
-      if (sms / div >= 2) tune_grid.push_back(sms / div);
-    for (int k = 1; k <= 4 && sms * k <= del_grid; ++k) tune_grid.push_back(sms * k);
+    if (common.deliver_blocks > 0) {
+      tune_grid.push_back(common.deliver_blocks);  // the schedule alone
+    } else {
+      // a few blocks for small networks (whose steps are all latency), up
+      // to four blocks per SM for large ones
+      for (int div : {8, 4, 2})
+        if (sms / div >= 2) tune_grid.push_back(sms / div);
+      for (int k = 1; k <= 4 && sms * k <= del_grid; ++k) tune_grid.push_back(sms * k);
+    }
     tune_at = (unsigned long long)common.autotune_at;
-    if (tune_grid.size() > 1) {
-      tune_ms.assign(2 * tune_grid.size(), 0.0);  // each grid, sequential and pipelined
+    const size_t n_sched = fixed_schedule == DBNET_SCHEDULE_AUTO ? 3 : 1;
+    if (tune_grid.size() * n_sched > 1) {
+      tune_ms.assign(3 * tune_grid.size(), 0.0);  // each grid on each schedule
       tune_pending = true;
     }
   }
-  fixed_schedule = common.schedule;
-  pipelined = common.schedule == DBNET_SCHEDULE_PIPELINED;
   CK(cudaGetLastError());
 }
 
@@ -810,30 +827,35 @@ int64_t Engine::tune_emit(int64_t n) {
 }
 
 // Up to n steps of the launch-shape tuner: the candidates -- a delivery grid
-// and the sequential or the pipelined schedule -- take turns, kTuneRounds
-// times each, every turn one captured chunk of kChunk steps between two
-// events (captured beforehand, so the timing is the device's); the
+// and the sequential, pipelined or persistent schedule -- take turns,
+// kTuneRounds times each, every turn one chunk of kChunk steps between two
+// events (a captured graph, or one persistent launch, enqueued at once, so
+// the timing is the device's); the
 // smallest total wins, so that the network's own fluctuations of activity
 // from chunk to chunk average out.  Fewer than kChunk steps run plainly and
 // the tuning goes on at the next call.  Returns the steps run.
 int64_t Engine::tune_steps(int64_t n) {
-  const int C = (int)tune_grid.size() * 2;
+  const int C = (int)tune_grid.size() * 3;
   const int c = tune_done % C;
   if (n < kChunk) {
     for (int64_t i = 0; i < n; ++i) direct_step();
     return n;
   }
-  if (fixed_schedule != DBNET_SCHEDULE_AUTO && (c % 2 == 1) != (fixed_schedule == DBNET_SCHEDULE_PIPELINED)) {
-    tune_ms[(size_t)c] = 1e30;  // the other schedule is not a candidate
+  const int sched = c % 3, grid = tune_grid[(size_t)(c / 3)];
+  if ((fixed_schedule != DBNET_SCHEDULE_AUTO && sched + 1 != fixed_schedule) ||
+      (sched == 2 && grid > persist_max) || tune_ms[(size_t)c] >= kDropped) {
+    // not a candidate (another schedule, too many blocks to be co-resident),
+    // or dropped after the first round
+    tune_ms[(size_t)c] = kDropped;
     finish_turn(C);
     return 0;
   }
-  set_shape(tune_grid[(size_t)(c / 2)], c % 2 == 1);
+  set_shape(grid, sched);
   if (!pipelined && long_pending) {
     direct_step();
     return 1;
   }
-  if (!gexec) capture();
+  if (!gexec && !persistent) capture();
   if (pipelined && !long_pending) {
     launch_deliver(dev, del_grid, StepRef{nullptr, g_host, nullptr}, stream, kPartLong);
     long_pending = true;
@@ -854,20 +876,26 @@ int64_t Engine::tune_steps(int64_t n) {
 }
 
 void Engine::finish_turn(int C) {
-  if (++tune_done < C * kTuneRounds) return;
+  if (++tune_done == C) {  // after the first round, drop the candidates over twice the best
+    const double best = *std::min_element(tune_ms.begin(), tune_ms.end());
+    for (double& t : tune_ms)
+      if (t > 2.0 * best) t = kDropped;
+  }
+  if (tune_done < C * kTuneRounds) return;
   int best = 0;
   for (int k = 1; k < C; ++k)
     if (tune_ms[(size_t)k] < tune_ms[(size_t)best]) best = k;
-  set_shape(tune_grid[(size_t)(best / 2)], best % 2 == 1);
+  set_shape(tune_grid[(size_t)(best / 3)], best % 3);
   tune_pending = false;
 }
 
 
 
-void Engine::set_shape(int grid, bool pip) {
-  if (grid == del_grid && pip == pipelined) return;
+void Engine::set_shape(int grid, int sched) {
+  if (grid == del_grid && (sched == 1) == pipelined && (sched == 2) == persistent) return;
   del_grid = grid;
-  pipelined = pip;
+  pipelined = sched == 1;
+  persistent = sched == 2;
   if (gexec) {
     CK(cudaStreamSynchronize(stream));
     CK(cudaGraphExecDestroy(gexec));
@@ -878,6 +906,19 @@ void Engine::set_shape(int grid, bool pip) {
 // n steps with the current delivery grid: whole chunks from the captured
 // graph, the rest as direct launches
 void Engine::run_plain(int64_t n) {
+  if (persistent) {  // the pending long part first, then whole launches
+    if (n > 0 && long_pending) {
+      direct_step();
+      --n;
+    }
+    while (n > 0) {
+      const int k = (int)std::min<int64_t>(n, kPersistSteps);
+      CK(launch_persist(dev, del_grid, g_host, k, pbar.p, kBarrierLimitNs, stream));
+      g_host += (unsigned long long)k;
+      n -= k;
+    }
+    return;
+  }
   if (n >= kChunk && !pipelined && long_pending) {  // the pending long part first
     direct_step();
     --n;
@@ -953,6 +994,11 @@ void Engine::sync() {
   CK(cudaStreamSynchronize(stream));
   unsigned f = 0;
   CK(cudaMemcpy(&f, flags.p, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f & kFlagTimeout) {
+    poisoned = true;
+    poison_msg = "a grid barrier of the persistent stepper timed out";
+    raise(DBNET_ETIMEOUT, poison_msg);
+  }
   if (f & kFlagHistOverflow)
     raise(DBNET_ERANGE, "spike ring overflowed its capacity");
 }
@@ -1027,6 +1073,25 @@ int dbnet_abi_sizes(int64_t* out, int n) {
   if (!out && n > 0) return DBNET_EINVAL;
   for (int k = 0; k < n && k < 11; ++k) out[k] = sz[k];
   return 10;
+}
+
+int dbnet_barrier_probe(int32_t blocks, int32_t missing, int32_t rounds, int64_t limit_us) {
+  return guarded(nullptr, [&] {
+    int dev_id = 0, sms = 0;
+    CK(cudaGetDevice(&dev_id));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+    if (blocks < 1 || blocks > sms || missing < 0 || rounds < 1 || limit_us < 1 || limit_us > 10000000)
+      raise(DBNET_EINVAL, "barrier probe: blocks in 1..SMs, missing >= 0, rounds >= 1, limit_us in 1..1e7");
+    DevBuf<unsigned> w;  // the barrier's count and the flags word
+    w.alloc(2);
+    CK(cudaMemset(w.p, 0, 2 * sizeof(unsigned)));
+    CK(launch_barrier_probe(blocks, (unsigned)missing, rounds, (unsigned long long)limit_us * 1000ull,
+                            w.p, w.p + 1, nullptr));
+    CK(cudaStreamSynchronize(nullptr));
+    unsigned f = 0;
+    CK(cudaMemcpy(&f, w.p + 1, sizeof(f), cudaMemcpyDeviceToHost));
+    if (f & kFlagTimeout) raise(DBNET_ETIMEOUT, "the grid barrier's wait gave up at its limit");
+  });
 }
 
 int dbnet_set_allocator(const dbnet_allocator_t* a) {
@@ -1266,7 +1331,8 @@ int dbnet_stats(dbnet_t* h, dbnet_stats_t* out) {
     out->deliver_blocks = e.del_grid;
     out->seg_ring = ih.graph->seg_kind == kSeg16 ? (int32_t)e.dev.seg_cap : 0;
     out->emit_delay = e.dev.d_emit <= e.dev.D ? e.dev.d_emit : 0;
-    out->pipelined = e.pipelined ? 1 : 0;
+    out->schedule = e.persistent ? DBNET_SCHEDULE_PERSISTENT
+                   : e.pipelined ? DBNET_SCHEDULE_PIPELINED : DBNET_SCHEDULE_SEQUENTIAL;
     out->autotuned = (!e.tune_pending && !e.tune_grid.empty()) ? 1 : 0;
     out->two_weights = e.dev.four;
   });

@@ -161,6 +161,7 @@ struct StepRef {
 
 enum : unsigned {
   kFlagHistOverflow = 1u,  // a spike did not fit its ring slot (cannot happen: a slot holds every neuron)
+  kFlagTimeout = 2u,       // a grid barrier of the persistent stepper gave up waiting
 };
 
 struct EngineDev {
@@ -211,6 +212,20 @@ void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s, in
 void launch_close(const EngineDev& e, unsigned long long g, cudaStream_t s);
 void launch_set_base(unsigned long long* base, unsigned long long g, cudaStream_t s);
 int deliver_grid();
+// The persistent stepper: iterations g0 .. g0 + nsteps - 1 (every part of
+// the delivery, then the update, per iteration) in one cooperative launch
+// of grid blocks, which must not exceed persist_max_grid(e) (0: the
+// occupancy query failed).  *count is the grid barrier's word, cleared on s
+// before the launch; each barrier wait gives up after limit_ns and sets
+// kFlagTimeout in e.flags.  Returns the launch's error code.
+int persist_max_grid(const EngineDev& e);
+cudaError_t launch_persist(const EngineDev& e, int grid, unsigned long long g0, int nsteps,
+                           unsigned* count, unsigned long long limit_ns, cudaStream_t s);
+// The grid barrier alone: rounds barriers over grid blocks of one
+// cooperative launch, each expecting extra arrivals more than the grid
+// makes (extra > 0: the first wait runs out and sets kFlagTimeout in *flags).
+cudaError_t launch_barrier_probe(int grid, unsigned extra, int rounds, unsigned long long limit_ns,
+                                 unsigned* count, unsigned* flags, cudaStream_t s);
 void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,
                    const int32_t* col_in, const void* w_in, const void* w2_in, int32_t w_dtype,
                    const uint8_t* delay_in, uint16_t* rec, int32_t dmax, int32_t seg_stride,

@@ -249,10 +249,11 @@ struct Engine {
   EngineDev dev{};
   cudaGraphExec_t gexec = nullptr;
   int del_grid = 0;
-  // launch-shape autotuner: from iteration tune_at on, one captured chunk
-  // per candidate (delivery grid x sequential or pipelined schedule), timed
-  // by CUDA events; the fastest stays and the step graph is captured again
+  // launch-shape autotuner: from iteration tune_at on, one chunk per
+  // candidate (delivery grid x sequential, pipelined or persistent
+  // schedule), timed by CUDA events; the fastest stays
   static constexpr int kTuneRounds = 3;
+  static constexpr double kDropped = 1e30;  // tune_ms of a candidate out of the running
   bool tune_pending = false;
   unsigned long long tune_at = 0;
   int tune_done = 0;                  // steps timed so far
@@ -267,8 +268,17 @@ struct Engine {
   bool pipelined = false;
   bool long_pending = false;
   int32_t fixed_schedule = 0;         // DBNET_SCHEDULE_*
+  // persistent schedule: up to kPersistSteps steps per cooperative launch
+  // of del_grid blocks (at most persist_max co-resident), pbar the grid
+  // barrier's word; a barrier wait gives up after kBarrierLimitNs
+  static constexpr int kPersistSteps = 4096;
+  static constexpr unsigned long long kBarrierLimitNs = 1000000000ull;
+  bool persistent = false;
+  int persist_max = 0;
+  DevBuf<unsigned> pbar;
   void direct_step();
-  void set_shape(int grid, bool pipelined);
+  // sched: 0 sequential, 1 pipelined, 2 persistent
+  void set_shape(int grid, int sched);
   void finish_turn(int n_candidates);
   // emission threshold: the engine's current d_emit (D + 1: none) and the
   // candidate the tuner weighs against "none" (0: no ring, nothing to tune).

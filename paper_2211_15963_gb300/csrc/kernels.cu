@@ -226,13 +226,14 @@ __device__ __forceinline__ float normal_from_word(unsigned long long w) {
 // OU current and the per-neuron injected-current factor.  FOUR: the
 // accumulators hold four channels per neuron (two weights per edge); the
 // background drive adds to both AMPA and NMDA.
+//
+// One tile of the iteration sr names; the block's threads call it together.
 template <bool EXT, bool FOUR>
-__global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef sr) {
+__device__ __forceinline__ void update_tile(const EngineDev& e, const StepRef& sr, int tile) {
   __shared__ RegionConst s_rc[kTileRegions];
   __shared__ uint32_t s_wtot[kUpdThreads / 32];
   __shared__ uint32_t s_hbase;
   __shared__ unsigned long long s_rbase;
-  const int tile = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // state loads first: they depend only on the tile, and the arrays cover
   // every padded tile
@@ -443,6 +444,11 @@ __global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef 
   }
 }
 
+template <bool EXT, bool FOUR>
+__global__ void __launch_bounds__(kUpdThreads, 4) k_update(EngineDev e, StepRef sr) {
+  update_tile<EXT, FOUR>(e, sr, blockIdx.x);
+}
+
 __device__ __forceinline__ uint32_t edge_delay(const uint32_t* col, const uint8_t* dl, int shift,
                                                int64_t e) {
   return dl ? (uint32_t)__ldg(dl + e) : (__ldg(col + e) >> shift);
@@ -483,8 +489,21 @@ struct ItemLoads {
 // iteration g - 1; then kPartShort after that update: the bin close, the
 // ring bookkeeping, the segment-ring copy of step g - 1's spikes, the
 // delay-1 items and the emission items.
-template <bool FOUR, bool SINGLE>
-__global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef sr, int part) {
+// Loads of the spike and segment rings: through the read-only path when
+// the rings are written only by earlier launches; from the L2 (coherent,
+// never a stale L1 line) in the persistent stepper, whose own blocks wrote
+// them earlier in the launch.
+template <bool PERSIST, typename T>
+__device__ __forceinline__ T ld_ring(const T* p) {
+  if (PERSIST) return __ldcg(p);
+  return __ldg(p);
+}
+
+// The delivery of the iteration sr names, as block bid of nblk; the block's
+// threads call it together.
+template <bool FOUR, bool SINGLE, bool PERSIST>
+__device__ __forceinline__ void deliver_body(const EngineDev& e, const StepRef& sr, int part, int bid,
+                                             int nblk) {
   // arrival items of phase q and delay bucket i start at s_phase[q] +
   // s_pre[q][i]; bucket i holds ranks [q c/Q, (q+1) c/Q) of the c spikes
   // handed on at g - i - 1
@@ -499,11 +518,11 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
   const unsigned long long g = step_of(sr);
   const int D = e.D;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gtid = bid * blockDim.x + threadIdx.x;
   // close the bin that ended with the previous iteration, one region per thread
   const bool do_short = part != kPartLong, do_long = part != kPartShort;
   if (do_short)
-    for (int gr = gtid; gr < e.total_R; gr += gridDim.x * blockDim.x) close_region(e, gr, g);
+    for (int gr = gtid; gr < e.total_R; gr += nblk * blockDim.x) close_region(e, gr, g);
   // the slot that the updates from this iteration on fill (a bin later with
   // spike binning) was last read by the previous iteration; the slot handed
   // on at g - 1 gets its long delays now, at emission, when d_emit allows
@@ -525,10 +544,10 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
     if (c1 > (unsigned long long)e.seg_cap) c1 = (unsigned long long)e.seg_cap;
     const unsigned long long want = (c1 + kSegGroup - 1) / kSegGroup;
     // at most a 32nd of the grid: the copy overlaps the item blocks' work
-    const int most = gridDim.x >= 64 ? (int)gridDim.x / 32 : 1;  // the host launches >= 2 blocks
+    const int most = nblk >= 64 ? nblk / 32 : 1;  // the host launches >= 2 blocks
     nA = want < (unsigned long long)most ? (int)want : most;
   }
-  if ((int)blockIdx.x < nA) {
+  if (bid < nA) {
     // Groups of 32 spikes: their segment-table rows are loaded at once (one
     // 16-byte vector of 8 delays per task, consecutive lanes on consecutive
     // spikes), transposed in shared memory to [delay][spike], and stored
@@ -536,7 +555,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
     const size_t cap = (size_t)e.seg_cap;
     const int dcap = e.dcap;
     const int nq_all = (planes + 7) >> 3;
-    for (unsigned long long k0 = (unsigned long long)blockIdx.x * kSegGroup; k0 < c1;
+    for (unsigned long long k0 = (unsigned long long)bid * kSegGroup; k0 < c1;
          k0 += (unsigned long long)nA * kSegGroup) {
       if (threadIdx.x < kSegGroup) {
         const unsigned long long k = k0 + threadIdx.x;
@@ -544,7 +563,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
         int nq = 0;
         long long r0 = 0;
         if (k < c1) {
-          const uint32_t ent = e.hist[s1 * (unsigned long long)e.hist_cap + k];
+          const uint32_t ent = ld_ring<PERSIST>(e.hist + s1 * (unsigned long long)e.hist_cap + k);
           const int64_t gidx = (int64_t)(ent & 0x7FFFFFFFu);
           const int inst = SINGLE ? 0 : e.tile_info[gidx / kTile].x;
           if (inst >= 0) {
@@ -584,7 +603,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
     }
     return;
   }
-  const int bB = (int)blockIdx.x - nA, nB = (int)gridDim.x - nA;  // item blocks
+  const int bB = bid - nA, nB = nblk - nA;  // item blocks
 
   // spikes handed on at step g - d for d = threadIdx.x + 1, and their
   // exclusive prefix (delays up to D - 1 - bin_lead: the later slots hold
@@ -671,7 +690,7 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
       p.d = (uint32_t)e.d_emit + (uint32_t)(te % (unsigned long long)ne);
       p.slot = (uint32_t)s1;
       p.aslot = (uint32_t)((g - 1ull + p.d) % (unsigned long long)e.acc_slots);
-      p.ent = __ldg(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
+      p.ent = ld_ring<PERSIST>(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
       return;
     }
     p.aslot = aslot_now;
@@ -687,13 +706,13 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
     p.d = (uint32_t)lo + 1u;
     p.k = (uint32_t)((unsigned long long)q * s_cnt[lo] / (unsigned long long)Q + (tq - s_pre[q][lo]));
     p.slot = (uint32_t)((g - p.d) % (unsigned long long)D);
-    p.ent = __ldg(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
+    p.ent = ld_ring<PERSIST>(e.hist + (size_t)p.slot * (size_t)e.hist_cap + p.k);
     if (p.d >= 2u && p.k < cap) {  // from the delay-major ring (coalesced across lanes)
       p.ring = true;
-      p.r0 = __ldg(e.hr0 + p.slot * cap + p.k);
+      p.r0 = ld_ring<PERSIST>(e.hr0 + p.slot * cap + p.k);
       const uint16_t* H = e.hseg + ((size_t)p.slot * (size_t)e.dcap) * cap + p.k;
-      p.a = __ldg(H + (size_t)(p.d - 2u) * cap);
-      p.b = __ldg(H + (size_t)(p.d - 1u) * cap);
+      p.a = ld_ring<PERSIST>(H + (size_t)(p.d - 2u) * cap);
+      p.b = ld_ring<PERSIST>(H + (size_t)(p.d - 1u) * cap);
     }
   };
   // stage two: the item's edge segment [e0, e0 + nseg) from the stage-one
@@ -841,6 +860,94 @@ __global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(kFull, ev, o);
   if (lane == 0 && ev) atomicAdd(e.events, ev);
+}
+
+template <bool FOUR, bool SINGLE>
+__global__ void __launch_bounds__(kDelThreads, 4) k_deliver(EngineDev e, StepRef sr, int part) {
+  deliver_body<FOUR, SINGLE, false>(e, sr, part, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch.  Thread 0 of every block adds
+// one to *count after a device-scope fence and waits until the count
+// reaches target (the blocks of the grid times the barriers passed,
+// counting this one); the block's other threads wait at the block barriers
+// on both sides.  The wait is bounded: after limit_ns of the global timer,
+// or as soon as another block has given up (kFlagTimeout set in *flags), it
+// gives up too, sets kFlagTimeout, and every thread of the block gets false.
+__device__ bool grid_barrier(unsigned* count, unsigned target, unsigned long long limit_ns,
+                             unsigned* flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    while ((int)(ld_acquire_u32(count) - target) < 0) {
+      if (*reinterpret_cast<volatile unsigned*>(flags) & kFlagTimeout) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > limit_ns) {
+        atomicOr(flags, kFlagTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The persistent stepper: iterations g0 .. g0 + nsteps - 1 in one
+// cooperative launch, each the delivery (the whole grid, as in k_deliver)
+// and the update (tiles dealt round robin over the blocks), with a grid
+// barrier after each.  The same device functions as the two-launch step do
+// the work, so the results are identical bit for bit; a barrier that gives
+// up ends the launch (kFlagTimeout stays set for the host).
+template <bool EXT, bool FOUR, bool SINGLE>
+__global__ void __launch_bounds__(kDelThreads, 2)
+    k_persist(EngineDev e, unsigned long long g0, int nsteps, unsigned* count,
+              unsigned long long limit_ns) {
+  unsigned target = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    const StepRef sr{nullptr, g0 + (unsigned long long)s, nullptr};
+    deliver_body<FOUR, SINGLE, true>(e, sr, kPartAll, blockIdx.x, gridDim.x);
+    target += gridDim.x;
+    if (!grid_barrier(count, target, limit_ns, e.flags)) return;
+    for (int t = blockIdx.x; t < e.n_tiles; t += gridDim.x) {
+      __syncthreads();  // the previous tile's block-shared values are read
+      update_tile<EXT, FOUR>(e, sr, t);
+    }
+    target += gridDim.x;
+    if (!grid_barrier(count, target, limit_ns, e.flags)) return;
+  }
+}
+
+// The grid barrier alone, rounds times, with extra arrivals expected per
+// round that no block makes when extra > 0 (the wait then runs out).
+__global__ void k_barrier_probe(unsigned* count, unsigned extra, int rounds,
+                                unsigned long long limit_ns, unsigned* flags) {
+  unsigned target = 0;
+  for (int r = 0; r < rounds; ++r) {
+    target += gridDim.x + extra;
+    if (!grid_barrier(count, target, limit_ns, flags)) return;
+  }
 }
 
 // BF16 bit pattern of staged weight e (float32 rounded to nearest even, or
@@ -1014,6 +1121,55 @@ void launch_deliver(const EngineDev& e, int grid, StepRef sr, cudaStream_t s, in
     if (e.four) k_deliver<true, false><<<grid, kDelThreads, 0, s>>>(e, sr, part);
     else k_deliver<false, false><<<grid, kDelThreads, 0, s>>>(e, sr, part);
   }
+}
+
+int persist_max_grid(const EngineDev& e) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* f = e.four ? (e.any_ext ? (const void*)k_persist<true, true, false>
+                                      : (const void*)k_persist<false, true, false>)
+                         : (e.any_ext ? (const void*)k_persist<true, false, false>
+                                      : (const void*)k_persist<false, false, false>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, kDelThreads, 0) != cudaSuccess) return 0;
+  return sms * occ;
+}
+
+template <bool EXT, bool FOUR, bool SINGLE>
+static cudaError_t coop_persist(const EngineDev& e, int grid, unsigned long long g0, int nsteps,
+                                unsigned* count, unsigned long long limit_ns, cudaStream_t s) {
+  EngineDev ea = e;
+  void* args[] = {&ea, &g0, &nsteps, &count, &limit_ns};
+  return cudaLaunchCooperativeKernel(k_persist<EXT, FOUR, SINGLE>, dim3(grid), dim3(kDelThreads),
+                                     args, 0, s);
+}
+
+cudaError_t launch_persist(const EngineDev& e, int grid, unsigned long long g0, int nsteps,
+                           unsigned* count, unsigned long long limit_ns, cudaStream_t s) {
+  if (grid < 2) grid = 2;  // with a segment ring, block 0 may take no items
+  cudaError_t r = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+  if (r != cudaSuccess) return r;
+  const bool one = e.n_inst == 1;
+  if (e.four) {
+    if (e.any_ext)
+      return one ? coop_persist<true, true, true>(e, grid, g0, nsteps, count, limit_ns, s)
+                 : coop_persist<true, true, false>(e, grid, g0, nsteps, count, limit_ns, s);
+    return one ? coop_persist<false, true, true>(e, grid, g0, nsteps, count, limit_ns, s)
+               : coop_persist<false, true, false>(e, grid, g0, nsteps, count, limit_ns, s);
+  }
+  if (e.any_ext)
+    return one ? coop_persist<true, false, true>(e, grid, g0, nsteps, count, limit_ns, s)
+               : coop_persist<true, false, false>(e, grid, g0, nsteps, count, limit_ns, s);
+  return one ? coop_persist<false, false, true>(e, grid, g0, nsteps, count, limit_ns, s)
+             : coop_persist<false, false, false>(e, grid, g0, nsteps, count, limit_ns, s);
+}
+
+cudaError_t launch_barrier_probe(int grid, unsigned extra, int rounds, unsigned long long limit_ns,
+                                 unsigned* count, unsigned* flags, cudaStream_t s) {
+  cudaError_t r = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+  if (r != cudaSuccess) return r;
+  void* args[] = {&count, &extra, &rounds, &limit_ns, &flags};
+  return cudaLaunchCooperativeKernel(k_barrier_probe, dim3(grid), dim3(32), args, 0, s);
 }
 
 void launch_ingest(int32_t N, int32_t j0, int32_t j1, int64_t e_base, const int64_t* row_ptr,

@@ -31,7 +31,8 @@ DBNET_ERANGE = -7
 DBNET_EUNSUPPORTED = -8
 DBNET_WEIGHT_F32 = 0
 DBNET_WEIGHT_BF16 = 1
-DBNET_SCHEDULE_AUTO, DBNET_SCHEDULE_SEQUENTIAL, DBNET_SCHEDULE_PIPELINED = 0, 1, 2
+DBNET_SCHEDULE_AUTO, DBNET_SCHEDULE_SEQUENTIAL, DBNET_SCHEDULE_PIPELINED, DBNET_SCHEDULE_PERSISTENT = \
+    0, 1, 2, 3
 DBENS_DIFFUSION = 0
 DBENS_GLOBAL = 1
 
@@ -66,7 +67,7 @@ class dbnet_options_t(ctypes.Structure):
                 ("bw_rho", _d), ("bw_V0", _d), ("seed", _u64), ("net_id", _u64),
                 ("fixed_shift", _i32), ("precision", _i32), ("raster_capacity", _i64),
                 ("bold_capacity", _i64), ("autotune_at", _i64), ("bin_spikes", _i32),
-                ("emit_delay", _i32), ("schedule", _i32), ("reserved_opt", _i32)]
+                ("emit_delay", _i32), ("schedule", _i32), ("deliver_blocks", _i32)]
 
 
 class dbnet_stats_t(ctypes.Structure):
@@ -74,7 +75,7 @@ class dbnet_stats_t(ctypes.Structure):
                 ("raster_dropped", _i64), ("bold_samples", _i64), ("fixed_shift", _i32),
                 ("max_delay", _i32), ("packed_edges", _i32), ("weights_rounded", _i32),
                 ("deliver_blocks", _i32), ("autotuned", _i32), ("two_weights", _i32),
-                ("seg_ring", _i32), ("emit_delay", _i32), ("pipelined", _i32)]
+                ("seg_ring", _i32), ("emit_delay", _i32), ("schedule", _i32)]
 
 
 class dbnet_device_graph_t(ctypes.Structure):
@@ -123,6 +124,7 @@ _SIGS = {
     "dbnet_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dbnet_last_error": (ctypes.c_char_p, []),
     "dbnet_set_allocator": (ctypes.c_int, [ctypes.POINTER(dbnet_allocator_t)]),
+    "dbnet_barrier_probe": (ctypes.c_int, [_i32, _i32, _i32, _i64]),
     "dbnet_abi_sizes": (ctypes.c_int, [_vp, ctypes.c_int]),
     "dbnet_options_default": (ctypes.c_int, [ctypes.POINTER(dbnet_options_t)]),
     "dbnet_create": (ctypes.c_int, [ctypes.POINTER(dbnet_graph_t), _vp,
@@ -233,6 +235,19 @@ def _stream(stream) -> int:
     if hasattr(stream, "cuda_stream"):
         return int(stream.cuda_stream)
     return int(stream)
+
+
+def dbnet_barrier_probe(blocks: int, missing: int = 0, rounds: int = 1,
+                        limit_us: int = 1_000_000) -> int:
+    """One cooperative launch of the persistent stepper's grid barrier on
+    the current device: `rounds` barriers over `blocks` blocks, each
+    expecting `missing` arrivals more than the grid makes.  Returns the
+    status code: DBNET_OK, or DBNET_ETIMEOUT when a wait gave up at
+    limit_us (always, for missing > 0); raises DbnetError for others."""
+    rc = lib().dbnet_barrier_probe(int(blocks), int(missing), int(rounds), int(limit_us))
+    if rc not in (DBNET_OK, DBNET_ETIMEOUT):
+        raise DbnetError(rc, "dbnet_barrier_probe")
+    return rc
 
 
 # ------------------------------------------------------------- allocator ----

@@ -288,15 +288,16 @@ def test_one_millisecond_step_without_delays():
     assert np.allclose(net.bold(), o.bold(), rtol=1e-10, atol=1e-15)
 
 
-def test_ou_current_without_noise_bit_exact():
+@pytest.mark.parametrize("schedule", [0, 3])
+def test_ou_current_without_noise_bit_exact(schedule):
     """Background OU current with sigma = 0 (Eq. 1 without the noise term):
     deterministic relaxation of I_bg from a chosen start, inside the
     membrane bracket -- matched-FP32 bit-exact, I_bg included.  One region
-    has the current, one does not."""
+    has the current, one does not.  Also on the persistent stepper (3)."""
     g = synth.make_graph([1800, 1300], 80, 61, d_within=(1, 25), d_cross=(25, 70))
     p = [synth.default_region_params(I_ext=0.6, ou_mu=0.35, ou_sigma=0.0, ou_tau=8.0),
          synth.default_region_params()]
-    net = _net(g, p, seed=12)
+    net = _net(g, p, seed=12, schedule=schedule)
     o = oracle.Sim(g, p, seed=12, precision=32)
     I0 = np.random.default_rng(5).uniform(-0.5, 1.0, g.n_neurons).astype(np.float32)
     net.set_ibg(I0)
@@ -399,16 +400,18 @@ def test_lowered_fixed_point_scale_bit_exact():
 
 
 # ------------------------------------------------ two weights per edge -----
-def test_two_weights_per_edge_bit_exact():
+@pytest.mark.parametrize("schedule", [0, 3])
+def test_two_weights_per_edge_bit_exact(schedule):
     """Two weights per edge (Supplementary Table 5 keeps one per channel):
     AMPA / GABA_A take the first, NMDA / GABA_B the second.  On the device:
     four accumulator channels, 8-byte records, one 64-bit atomic per edge.
-    Uneven regions with a ragged tail, delays up to 120 steps."""
+    Uneven regions with a ragged tail, delays up to 120 steps.  Also on the
+    persistent stepper (3)."""
     g = synth.with_second_weight(
         synth.make_graph([1500, 700, 333, 2049], 80, 21, k_within=64, d_within=(1, 30),
                          d_cross=(30, 120)), 77)
     params = [synth.default_region_params(I_ext=0.8 + 0.05 * r) for r in range(g.n_regions)]
-    net = _net(g, params, seed=4, tr_ms=5.0)
+    net = _net(g, params, seed=4, tr_ms=5.0, schedule=schedule)
     o = oracle.Sim(g, params, seed=4, tr_ms=5.0, precision=32)
     s = net.stats()
     assert s["two_weights"] == 1 and s["packed_edges"] == 1
@@ -586,17 +589,18 @@ def test_row_with_65536_out_edges_uses_u32_segment_counts():
     net.close()
 
 
-@pytest.mark.parametrize("bin_ms", [1.0, 0.5])
-def test_spike_binning_bit_exact(bin_ms):
+@pytest.mark.parametrize("bin_ms,schedule", [(1.0, 0), (0.5, 0), (1.0, 3)])
+def test_spike_binning_bit_exact(bin_ms, schedule):
     """Supplementary Sec. 3: spikes handed on at bin edges (b_t = 1 ms and
     0.5 ms at dt = 0.1 ms) on a ragged multi-region network with cross-region
     delays; raster, state, BOLD and the synaptic events equal the
-    matched-FP32 oracle with the same binning over 200 ms."""
+    matched-FP32 oracle with the same binning over 200 ms (also on the
+    persistent stepper, 3)."""
     g = synth.make_graph([3000, 1500, 2500], 100, 41, k_within=80, d_within=(1, 30),
                          d_cross=(30, 90))
     p = [synth.default_region_params(I_ext=0.85 + 0.05 * r) for r in range(3)]
     spb = int(round(bin_ms / 0.1))
-    net = _net(g, p, seed=14, bin_ms=bin_ms, tr_ms=20.0, bin_spikes=1)
+    net = _net(g, p, seed=14, bin_ms=bin_ms, tr_ms=20.0, bin_spikes=1, schedule=schedule)
     ref = oracle.Sim(g, p, seed=14, bin_ms=bin_ms, tr_ms=20.0, precision=32, bin_spikes=True)
     net.step(2000)
     ref.step(2000)
@@ -743,21 +747,25 @@ def test_per_region_long_run_statistics_against_fp64_oracle():
     net.close()
 
 
-@pytest.mark.parametrize("schedule", [2, 1, 0])
-def test_pipelined_schedule_is_bit_exact(schedule):
-    """The pipelined schedule runs the delivery of step n + 1's delays >= 2
-    on a second stream beside the update of step n (double-buffered
-    accumulators), then the rest of step n + 1's delivery: the same
-    additions in another order, so raster, state, BOLD and events equal the
-    oracle's.  Step calls of 1, 63, 64, 200 and 333 steps mix graph replays
-    and direct steps; with the automatic schedule the tuner (from step 150)
-    switches between the two while steps are in flight."""
+@pytest.mark.parametrize("schedule", [3, 2, 1, 0])
+def test_step_schedules_are_bit_exact(schedule):
+    """The pipelined schedule (2) runs the delivery of step n + 1's delays
+    >= 2 on a second stream beside the update of step n (double-buffered
+    accumulators), then the rest of step n + 1's delivery; the persistent
+    stepper (3) runs up to 4,096 steps in one cooperative launch, the two
+    kernels' device code separated by grid barriers, the update's 7 tiles
+    dealt over the blocks.  The same additions in another order, so raster,
+    state, BOLD and events equal the oracle's.  Step calls of 1, 63, 64, 200
+    and 333 steps mix graph replays and direct steps (4,200 for the
+    persistent stepper: two launches); with the automatic schedule (0) the
+    tuner (from step 150) switches between the three while steps are in
+    flight."""
     g = synth.make_graph([2500, 1200, 3100], 90, 53, k_within=70, d_within=(1, 25),
                          d_cross=(25, 90))
     p = [synth.default_region_params(I_ext=0.86 + 0.04 * r) for r in range(3)]
     net = _net(g, p, seed=17, tr_ms=25.0, schedule=schedule, autotune_at=150)
     o = oracle.Sim(g, p, seed=17, tr_ms=25.0, precision=32)
-    for n in (1, 63, 64, 200, 333, 1, 1100):
+    for n in (1, 63, 64, 200, 333, 1, 1100) + ((4200,) if schedule == 3 else ()):
         net.step(n)
         o.step(n)
     _assert_same_state(net, o, "schedule %d" % schedule)
@@ -768,19 +776,20 @@ def test_pipelined_schedule_is_bit_exact(schedule):
     assert np.allclose(net.bold(), o.bold(), rtol=1e-10, atol=1e-15)
     s = net.stats()
     assert s["events"] == o.info()["events"]
-    if schedule:
-        assert s["pipelined"] == (1 if schedule == 2 else 0)
+    assert s["schedule"] == schedule if schedule else s["schedule"] in (1, 2, 3)
     net.close()
 
 
-def test_pipelined_ensemble_members_equal_single_networks():
-    """An ensemble (several instances in one engine) on the pipelined
-    schedule: each member equals a single network on the sequential one."""
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_scheduled_ensemble_members_equal_single_networks(schedule):
+    """An ensemble (several instances in one engine) on the pipelined (2) or
+    persistent (3) schedule: each member equals a single network on the
+    sequential one."""
     from paper_2211_15963_gb300 import dbnet
     g = synth.make_graph([900, 700], 60, 54, k_within=48, d_within=(1, 20), d_cross=(20, 50))
     base = [synth.default_region_params(I_ext=0.9) for _ in range(2)]
     theta = np.random.default_rng(4).uniform(-0.5, 0.5, (3, 2, 2))
-    ens = dbnet.Ensemble(g, base, 3, theta, dict(seed=8, net_id=40, schedule=2,
+    ens = dbnet.Ensemble(g, base, 3, theta, dict(seed=8, net_id=40, schedule=schedule,
                                                 raster_capacity=1 << 20))
     ens.step(700)
     for m in range(3):
@@ -798,3 +807,55 @@ def test_pipelined_ensemble_members_equal_single_networks():
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         net.close()
     ens.close()
+
+
+def test_grid_barrier_wait_gives_up_with_a_status():
+    """The persistent stepper's grid barrier: barriers that every block
+    reaches complete (DBNET_OK); a barrier that waits for one arrival more
+    than the grid makes (a count nothing raises) gives up after its limit
+    (2 ms of the global timer), every block returns, the call reports
+    DBNET_ETIMEOUT, and the device stays usable: a network stepped
+    afterwards on the persistent stepper equals the oracle."""
+    import time
+    from paper_2211_15963_gb300 import dbnet
+    assert dbnet.dbnet_barrier_probe(16, 0, 1000) == dbnet.DBNET_OK
+    t0 = time.perf_counter()
+    assert dbnet.dbnet_barrier_probe(16, 1, 3, limit_us=2000) == dbnet.DBNET_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert dbnet.dbnet_barrier_probe(2, 0, 10) == dbnet.DBNET_OK
+    with pytest.raises(dbnet.DbnetError):
+        dbnet.dbnet_barrier_probe(0, 0, 1)
+    g = synth.make_graph([1500, 900], 60, 62, d_within=(1, 20), d_cross=(20, 40))
+    p = synth.default_region_params()
+    net = _net(g, p, seed=18, schedule=3)
+    o = oracle.Sim(g, p, seed=18, precision=32)
+    net.step(300)
+    o.step(300)
+    _assert_same_state(net, o, "after the probe")
+    assert net.stats()["schedule"] == 3
+    net.close()
+
+
+@pytest.mark.parametrize("schedule,blocks", [(1, 40), (3, 19), (3, 2), (0, 77)])
+def test_fixed_delivery_grid(schedule, blocks):
+    """deliver_blocks fixes the delivery grid (the autotuner then weighs the
+    schedules alone, with schedule 0): any grid gives the oracle's results,
+    down to two blocks on the persistent stepper; one block, or more
+    blocks than can be co-resident on the persistent stepper, is refused."""
+    from paper_2211_15963_gb300 import dbnet
+    g = synth.make_graph([2100, 1700], 70, 63, d_within=(1, 20), d_cross=(20, 60))
+    p = synth.default_region_params()
+    net = _net(g, p, seed=19, schedule=schedule, deliver_blocks=blocks, autotune_at=100)
+    o = oracle.Sim(g, p, seed=19, precision=32)
+    for n in (90, 700):
+        net.step(n)
+        o.step(n)
+    _assert_same_state(net, o, "grid %d, schedule %d" % (blocks, schedule))
+    s = net.stats()
+    assert s["deliver_blocks"] == blocks
+    assert s["schedule"] == schedule if schedule else s["schedule"] in (1, 2, 3)
+    assert s["events"] == o.info()["events"]
+    net.close()
+    for bad in (dict(deliver_blocks=1), dict(deliver_blocks=1 << 19, schedule=3)):
+        with pytest.raises(dbnet.DbnetError):
+            _net(g, p, seed=19, **bad)
