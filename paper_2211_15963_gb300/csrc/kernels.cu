@@ -635,10 +635,12 @@ __device__ __forceinline__ void deliver_body(const EngineDev& e, const StepRef& 
   for (int q = 0; q < kMaxPhases; ++q) {
     own[q] = q < Q ? (q + 1ull) * c / (unsigned long long)Q - q * c / (unsigned long long)Q : 0ull;
     incl[q] = own[q];
+    if (q < Q) {  // block-uniform
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long t = __shfl_up_sync(kFull, incl[q], o);
-      if (lane >= o) incl[q] += t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(kFull, incl[q], o);
+        if (lane >= o) incl[q] += t;
+      }
     }
     if (lane == 31) s_wsum[q][warp] = incl[q];
   }
@@ -879,23 +881,29 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* a) {
   return v;
 }
 
-// Grid-wide barrier of a cooperative launch.  Thread 0 of every block adds
-// one to *count after a device-scope fence and waits until the count
-// reaches target (the blocks of the grid times the barriers passed,
-// counting this one); the block's other threads wait at the block barriers
-// on both sides.  The wait is bounded: after limit_ns of the global timer,
-// or as soon as another block has given up (kFlagTimeout set in *flags), it
-// gives up too, sets kFlagTimeout, and every thread of the block gets false.
+__device__ __forceinline__ void red_release_add_u32(unsigned* a, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch.  After a block barrier (which
+// orders the block's earlier writes before thread 0's), thread 0 of every
+// block adds one to *count with device-scope release semantics and polls it
+// with acquire loads until it reaches target (the blocks of the grid times
+// the barriers passed, counting this one); the block barrier after the wait
+// orders the block's later reads after the acquire.  The wait is bounded:
+// after limit_ns of the global timer, or as soon as another block has given
+// up (kFlagTimeout set in *flags), it gives up too, sets kFlagTimeout, and
+// every thread of the block gets false.
 __device__ bool grid_barrier(unsigned* count, unsigned target, unsigned long long limit_ns,
                              unsigned* flags) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
+    red_release_add_u32(count, 1u);
     int ok = 1;
     const unsigned long long t0 = global_ns();
-    while ((int)(ld_acquire_u32(count) - target) < 0) {
+    for (unsigned spin = 0; (int)(ld_acquire_u32(count) - target) < 0; ++spin) {
+      if ((spin & 15u) != 15u) continue;  // the flag and the clock every 16 polls
       if (*reinterpret_cast<volatile unsigned*>(flags) & kFlagTimeout) {
         ok = 0;
         break;
@@ -905,9 +913,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned target, unsigned long lon
         ok = 0;
         break;
       }
-      __nanosleep(32);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();

@@ -254,7 +254,7 @@ def test_autotuned_grid_gives_identical_results():
     p = synth.default_region_params()
     tuned = _net(g, p, seed=5, autotune_at=150)
     plain = _net(g, p, seed=5, autotune_at=-1)
-    for n in (100, 333, 700, 2500):  # tuning starts inside the second call
+    for n in (100, 333, 700, 2500, 2000):  # tuning starts inside the second call
         tuned.step(n)
         plain.step(n)
     st, sp = tuned.stats(), plain.stats()
