@@ -89,6 +89,8 @@ def parse_from(argv):
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--tune-at", type=int, default=2000,
                     help="Euler step at which the library tunes the delivery's launch shape")
+    ap.add_argument("--deliver-blocks", type=int, default=0,
+                    help="fix the delivery grid (0: automatic; profiling at a chosen grid)")
     ap.add_argument("--step-ms", type=float, default=1000.0,
                     help="biological time per benchmark step of the network workloads (ms); "
                          "shorter steps only for profiling runs")
@@ -339,6 +341,7 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
     t_gen = time.perf_counter() - t_gen
     params = params_for(args.rate, args.k_in)
     opts = dict(seed=seed + 1, net_id=rank, bin_spikes=1 if args.bin_spikes else 0,
+                deliver_blocks=getattr(args, "deliver_blocks", 0),
                 autotune_at=getattr(args, "tune_at", 2000))
 
     t_create = time.perf_counter()
@@ -536,6 +539,17 @@ def run_extras(args, stream, dev):
                   "k_deliver_us": kern["k_deliver"]["avg_us"],
                   "k_deliver_frac": kern["k_deliver"]["frac"],
                   "path_frac": m["roofline"]["path"]["frac"], "clocks": m["clocks"]}
+    # the mid-size network at the paper's other two mean rates
+    out["mid_rates"] = {}
+    for rate in (7, 30):
+        r_args = argparse.Namespace(**dict(vars(mid_args), rate=rate))
+        r = run_network(r_args, WORKLOAD_DIMS["mid"], stream, dev, 1, 0, rank_seed(0, False), 2, 1,
+                        0, 200, pageable=False)
+        out["mid_rates"]["%d_hz" % rate] = {
+            "value": r["value"], "unit": UNIT, "rtf": r["rtf"], "steps": 2, "warmup": 1,
+            "mean_rate_hz": r["mean_rate_hz"], "deliver_blocks": r["deliver_blocks"],
+            "schedule": r["schedule"], "path_frac": r["roofline"]["path"]["frac"],
+            "clocks": r["clocks"]}
     small_args = argparse.Namespace(**dict(vars(args), steps=3, warmup=2, profile_steps=2000))
     s = run_small(small_args, stream)
     out["small"] = {k: s[k] for k in ("config", "value", "unit", "rtf", "events_per_s",
