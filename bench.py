@@ -231,7 +231,7 @@ def kernels_sha():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def measured_traffic(kernel, summary="traffic_mid_network.md"):
+def measured_traffic(kernel, summary="traffic_mid_network_15hz.md"):
     """DRAM bytes per launch of `kernel` (ncu dram__bytes_read.sum +
     dram__bytes_write.sum) from a committed summary under profiles/ (the
     mid-size network's by default), when it was taken on the current kernel
@@ -390,8 +390,10 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
     two = args.two_weights
     upd_bytes = g.n_neurons * (UPDATE_BYTES_PER_NEURON_FOUR if two else UPDATE_BYTES_PER_NEURON)
     del_bytes = ev_per_launch * (DELIVER_BYTES_PER_EVENT_TWO if two else DELIVER_BYTES_PER_EVENT)
-    tag = "%s_%dhz%s" % ("large_network" if g.n_neurons >= 20_000_000 else "mid_network",
-                         args.rate, "_two_weights" if two else "")
+    # a traffic summary exists only for the two standard networks
+    sizes = {tuple(WORKLOAD_DIMS["large"]): "large_network", tuple(WORKLOAD_DIMS["mid"]): "mid_network"}
+    name = sizes.get((g.n_regions, g.n_neurons // max(g.n_regions, 1)), "other_network")
+    tag = "%s_%dhz%s" % (name, args.rate, "_two_weights" if two else "")
     kern = {
         "k_update": {"avg_us": 1e3 * t_upd / profile_steps, "algorithmic_bytes": upd_bytes,
                      "achieved_gbs": upd_bytes / (t_upd / profile_steps * 1e-3) / 1e9,
