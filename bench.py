@@ -308,11 +308,19 @@ def oracle_sample(args, dims, seconds=15.0, onset_steps=500):
                          onset_steps, threads)}
 
 
+# Arm "CPU part" numbers of /proc/cpuinfo (Arm's published MIDR part ids)
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+             "0xd49": "Arm Neoverse N2"}
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part")):
+            if line.lower().startswith("model name"):
                 return line.split(":", 1)[1].strip()
+            if line.lower().startswith("cpu part"):
+                part = line.split(":", 1)[1].strip()
+                return "%s (CPU part %s)" % (ARM_PARTS[part], part) if part in ARM_PARTS else part
     except OSError:
         pass
     import platform
