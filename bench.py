@@ -250,6 +250,30 @@ def measured_traffic(kernel, summary="traffic_mid_network_15hz.md"):
     return int(m.group(1)) if m else None
 
 
+def profiled_shape():
+    """Occupancy and issue figures of both kernels from the committed ncu
+    full sets (profiles/k_deliver_400k_grid608.md, k_update_400k.md), when
+    they were taken on the current kernel source, else None."""
+    import re
+    out = {}
+    for kernel, name, what in (("k_deliver", "k_deliver_400k_grid608.md", "608 blocks"),
+                               ("k_update", "k_update_400k.md", "391 tiles")):
+        try:
+            txt = open(os.path.join(ROOT, "profiles", name)).read()
+        except OSError:
+            return None
+        m = re.search(r"kernels\.cu sha256\[:16\]\s+([0-9a-f]+)", txt)
+        if not m or m.group(1) != kernels_sha():
+            return None
+        warps = re.search(r"^\| warps active[^|]*\| ([0-9.]+) %", txt, flags=re.M)
+        issue = re.search(r"^\| issue active \| ([0-9.]+) %", txt, flags=re.M)
+        if not warps or not issue:
+            return None
+        out[kernel] = {"warps_active_pct": float(warps.group(1)), "issue_active_pct": float(issue.group(1)),
+                       "source": "profiles/%s (ncu full set, 400,000 neurons, %s)" % (name, what)}
+    return out
+
+
 def peaks():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -426,7 +450,8 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
                              % (UPDATE_BYTES_PER_NEURON_FOUR if two else UPDATE_BYTES_PER_NEURON,
                                 DELIVER_BYTES_PER_EVENT_TWO if two else DELIVER_BYTES_PER_EVENT),
                      "achieved": step_bytes / (ms_per_step / n_step * 1e-3) / 1e9,
-                     "frac": step_bytes / (ms_per_step / n_step * 1e-3) / 1e9 / hbm}}
+                     "frac": step_bytes / (ms_per_step / n_step * 1e-3) / 1e9 / hbm},
+            "ncu_shape": profiled_shape()}
     stats = net.stats()
     net.close()
     del flush
