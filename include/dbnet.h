@@ -151,10 +151,14 @@ typedef struct {
  *                    automatic emit_delay candidate, first D + 64 steps
  *                    without and D + 64 with it, the last 64 of each timed,
  *                    the faster kept; then every launch shape -- a delivery
- *                    grid (an eighth, a quarter and half of the SMs, and 1..4
- *                    blocks per SM) on each schedule the schedule option
- *                    admits -- runs 64 steps timed by CUDA events, three
- *                    times each in turn, and the smallest total is kept.
+ *                    grid (1..4 blocks per SM, and for networks of at most
+ *                    two 1,024-neuron tiles per SM also an eighth, a quarter
+ *                    and half of the SMs) on each schedule the schedule
+ *                    option admits (the persistent one only while its blocks
+ *                    hold at most one tile each) -- runs 64 steps timed by
+ *                    CUDA events, three times each in turn (after the first
+ *                    round those over twice the best drop out), and the
+ *                    smallest total is kept.
  *                    Results depend on none of these choices (integer
  *                    accumulation).  Default 2000 (200 ms at dt 0.1 ms, past
  *                    the onset).

@@ -22,6 +22,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "dbnet.h"
@@ -45,6 +46,28 @@ AllocHook current_alloc_hook() {
 }
 
 // ---------------------------------------------------------------- graph ----
+// The largest byte of a[0..n): over the host's cores for large arrays (the
+// delays of a 2e10-edge graph are 20 GB).
+static unsigned max_byte(const uint8_t* a, int64_t n) {
+  constexpr int64_t kPer = int64_t(1) << 26;  // at least 64 MB per thread
+  const int64_t want = (n + kPer - 1) / kPer;
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<int64_t>(std::min(hw, 64), std::max<int64_t>(want, 1));
+  auto span_max = [a](int64_t b, int64_t e) {
+    unsigned m = 0;
+    for (int64_t i = b; i < e; ++i) m = std::max<unsigned>(m, a[i]);
+    return m;
+  };
+  if (nt <= 1) return span_max(0, n);
+  std::vector<unsigned> part((size_t)nt, 0u);
+  std::vector<std::thread> th;
+  const int64_t per = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] { part[(size_t)t] = span_max(std::min(n, t * per), std::min(n, (t + 1) * per)); });
+  for (auto& x : th) x.join();
+  return *std::max_element(part.begin(), part.end());
+}
+
 std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   if (!g) raise(DBNET_EINVAL, "graph is NULL");
   const int32_t N = g->n_neurons, R = g->n_regions;
@@ -73,8 +96,7 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   gd->ro_h.assign(g->region_offsets, g->region_offsets + R + 1);
   gd->nexc_h.assign(g->n_exc, g->n_exc + R);
   // the largest delay and row length fix the segment table's shape
-  unsigned dmax_h = 0;
-  for (int64_t e = 0; e < E; ++e) dmax_h = std::max<unsigned>(dmax_h, g->delay[e]);
+  const unsigned dmax_h = E > 0 ? max_byte(g->delay, E) : 0u;
   gd->max_delay = (int32_t)std::max(1u, dmax_h);
   int64_t max_out = 0;
   for (int32_t j = 0; j < N; ++j) max_out = std::max(max_out, g->row_ptr[j + 1] - g->row_ptr[j]);
@@ -540,12 +562,16 @@ void Engine::init_pool(int32_t n_inst, int64_t tiles, int32_t regions, int32_t D
     if (common.deliver_blocks > 0) {
       tune_grid.push_back(common.deliver_blocks);  // the schedule alone
     } else {
-      // a few blocks for small networks (whose steps are all latency), up
-      // to four blocks per SM for large ones
-      for (int div : {8, 4, 2})
-        if (sms / div >= 2) tune_grid.push_back(sms / div);
+      // a few blocks only for small networks (at most two tiles per SM),
+      // whose steps are all latency; 1..4 blocks per SM for every network
+      if (tiles <= 2 * (int64_t)sms)
+        for (int div : {8, 4, 2})
+          if (sms / div >= 2) tune_grid.push_back(sms / div);
       for (int k = 1; k <= 4 && sms * k <= del_grid; ++k) tune_grid.push_back(sms * k);
     }
+    // the persistent stepper only where its blocks hold at most one update
+    // tile each; with more tiles it lost every measured comparison
+    persist_tunable = tiles <= (int64_t)persist_max;
     tune_at = (unsigned long long)common.autotune_at;
     const size_t n_sched = fixed_schedule == DBNET_SCHEDULE_AUTO ? 3 : 1;
     if (tune_grid.size() * n_sched > 1) {
@@ -843,7 +869,7 @@ int64_t Engine::tune_steps(int64_t n) {
   }
   const int sched = c % 3, grid = tune_grid[(size_t)(c / 3)];
   if ((fixed_schedule != DBNET_SCHEDULE_AUTO && sched + 1 != fixed_schedule) ||
-      (sched == 2 && grid > persist_max) || tune_ms[(size_t)c] >= kDropped) {
+      (sched == 2 && (grid > persist_max || !persist_tunable)) || tune_ms[(size_t)c] >= kDropped) {
     // not a candidate (another schedule, too many blocks to be co-resident),
     // or dropped after the first round
     tune_ms[(size_t)c] = kDropped;

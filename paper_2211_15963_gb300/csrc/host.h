@@ -275,6 +275,7 @@ struct Engine {
   static constexpr unsigned long long kBarrierLimitNs = 1000000000ull;
   bool persistent = false;
   int persist_max = 0;
+  bool persist_tunable = false;  // the tuner may weigh the persistent schedule
   DevBuf<unsigned> pbar;
   void direct_step();
   // sched: 0 sequential, 1 pipelined, 2 persistent
