@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libdbnet.so")
 SOURCES = ["kernels.cu", "engine.cu", "ens.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-fopenmp",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 
@@ -55,6 +55,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = SO + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"])
+    subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread", "-lgomp"])
     os.replace(tmp, SO)
     return SO

@@ -14,6 +14,7 @@
 // a captured CUDA graph of kChunk steps; all per-step indices live in device
 // memory, so the same graph serves every chunk.
 #include <cuda_runtime.h>
+#include <omp.h>
 
 #include <algorithm>
 #include <climits>
@@ -67,6 +68,70 @@ static unsigned max_byte(const uint8_t* a, int64_t n) {
   for (auto& x : th) x.join();
   return *std::max_element(part.begin(), part.end());
 }
+
+// Host-to-device copies from pageable host memory through pinned slices:
+// the host's cores copy each slice into pinned memory while the DMA of the
+// previous slices runs (the driver's own path for pageable sources copies
+// on one thread); pinned sources are copied directly.
+class HostStager {
+ public:
+  static constexpr size_t kSlice = size_t(64) << 20;
+  static constexpr int kSlices = 4;
+  explicit HostStager(cudaStream_t s) : s_(s) {}
+  HostStager(const HostStager&) = delete;
+  HostStager& operator=(const HostStager&) = delete;
+  ~HostStager() {
+    for (int i = 0; i < kSlices; ++i) {
+      if (ev_[i]) {
+        cudaEventSynchronize(ev_[i]);  // its copy has left the slice
+        cudaEventDestroy(ev_[i]);
+      }
+      if (buf_[i]) cudaFreeHost(buf_[i]);
+    }
+  }
+  void copy(void* dst, const void* src, size_t n) {
+    if (n == 0) return;
+    cudaPointerAttributes at{};
+    const bool pinned = cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // clear a lookup failure on an unregistered pointer
+    if (pinned || n < kSlice) {
+      CK(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s_));
+      return;
+    }
+    if (!buf_[0]) {
+      for (int i = 0; i < kSlices; ++i) {
+        CK(cudaHostAlloc(&buf_[i], kSlice, cudaHostAllocDefault));
+        CK(cudaEventCreateWithFlags(&ev_[i], cudaEventDisableTiming));
+      }
+    }
+    const auto* from = static_cast<const unsigned char*>(src);
+    auto* to = static_cast<unsigned char*>(dst);
+    for (size_t o = 0; o < n; o += kSlice) {
+      const size_t m = std::min(kSlice, n - o);
+      const int b = next_;
+      next_ = (next_ + 1) % kSlices;
+      CK(cudaEventSynchronize(ev_[b]));  // the slice's previous copy is done
+      fill(static_cast<unsigned char*>(buf_[b]), from + o, m);
+      CK(cudaMemcpyAsync(to + o, buf_[b], m, cudaMemcpyHostToDevice, s_));
+      CK(cudaEventRecord(ev_[b], s_));
+    }
+  }
+
+ private:
+  static void fill(unsigned char* dst, const unsigned char* src, size_t m) {
+    const int nt = std::max(1, std::min(omp_get_num_procs(), 16));
+    const size_t per = ((m + nt - 1) / nt + 4095) & ~size_t(4095);
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (int t = 0; t < nt; ++t) {
+      const size_t lo = std::min(m, (size_t)t * per), hi = std::min(m, lo + per);
+      if (hi > lo) std::memcpy(dst + lo, src + lo, hi - lo);
+    }
+  }
+  cudaStream_t s_;
+  void* buf_[kSlices] = {};
+  cudaEvent_t ev_[kSlices] = {};
+  int next_ = 0;
+};
 
 std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
   if (!g) raise(DBNET_EINVAL, "graph is NULL");
@@ -146,19 +211,17 @@ std::shared_ptr<GraphDev> upload_graph(const dbnet_graph_t* g, cudaStream_t s) {
     w_st.alloc(cap * wsz);
     if (gd->two_w) w2_st.alloc(cap * wsz);
     d_st.alloc(cap);
+    HostStager stage(s);
     int32_t j0 = 0;
     while (j0 < N) {
       int32_t j1 = j0 + 1;
       while (j1 < N && g->row_ptr[j1 + 1] - g->row_ptr[j0] <= cap) ++j1;
       const int64_t e0 = g->row_ptr[j0], ne = g->row_ptr[j1] - e0;
       if (ne > 0) {
-        CK(cudaMemcpyAsync(col_st.p, g->col + e0, sizeof(int32_t) * ne, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(d_st.p, g->delay + e0, ne, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(w_st.p, static_cast<const uint8_t*>(g->weight) + e0 * wsz, ne * wsz,
-                           cudaMemcpyHostToDevice, s));
-        if (gd->two_w)
-          CK(cudaMemcpyAsync(w2_st.p, static_cast<const uint8_t*>(g->weight2) + e0 * wsz, ne * wsz,
-                             cudaMemcpyHostToDevice, s));
+        stage.copy(col_st.p, g->col + e0, sizeof(int32_t) * ne);
+        stage.copy(d_st.p, g->delay + e0, ne);
+        stage.copy(w_st.p, static_cast<const uint8_t*>(g->weight) + e0 * wsz, ne * wsz);
+        if (gd->two_w) stage.copy(w2_st.p, static_cast<const uint8_t*>(g->weight2) + e0 * wsz, ne * wsz);
         launch_ingest(N, j0, j1, e0, gd->row_ptr.p, col_st.p, w_st.p,
                       gd->two_w ? w2_st.p : nullptr, g->weight_dtype, d_st.p,
                       gd->rec.p, gd->max_delay, gd->seg_stride, gd->seg.p, gd->seg_kind, indeg.p,
