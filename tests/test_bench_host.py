@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the replica combination over
 ranks (run here as two gloo processes on the CPU), per-rank seeds, the
-reference arm's rank rule and the serving drive interpolation."""
+reference arm's rank rule, the serving drive interpolation, launch counts per
+schedule and the hash gating of the profile figures."""
 import json
 import os
 import socket
@@ -89,3 +90,48 @@ def test_matched_spikes_counts_reference_spikes_within_tolerance():
     assert bench.matched_spikes(ref_t, ref_i, t, i, 1.0) == 2
     assert bench.matched_spikes(ref_t, ref_i, t, i, 2.0) == 4
     assert bench.matched_spikes(ref_t, ref_i, ref_t, ref_i, 0.0) == 5
+
+
+def test_launch_count_per_schedule():
+    """Kernels launched by one dbnet_step call of n steps: graph replays of
+    64 steps (128 launches, 192 when pipelined, plus the long part launched
+    ahead), direct steps for the rest, the base word and the bin close; on
+    the persistent schedule one launch per 4,096 steps and the bin close."""
+    import bench
+    assert bench.launches_per_call(10_000, "sequential") == 156 * 128 + 16 * 2 + 2
+    assert bench.launches_per_call(10_000, "pipelined") == 156 * 192 + 16 * 2 + 2 + 1
+    assert bench.launches_per_call(63, "sequential") == 63 * 2 + 1
+    assert bench.launches_per_call(10_000, "persistent") == 3 + 1
+    assert bench.launches_per_call(4096, "persistent") == 1 + 1
+
+
+def test_profile_figures_follow_the_kernel_source(tmp_path, monkeypatch):
+    """The bench quotes traffic and occupancy from committed ncu summaries
+    only while they carry the current kernels.cu hash."""
+    import bench
+    sha = bench.kernels_sha()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic_x.md").write_text(
+        "kernels.cu sha256[:16]: %s\n\n| k_deliver | 123456 | a |\n" % sha)
+    (tmp_path / "profiles" / "traffic_old.md").write_text(
+        "kernels.cu sha256[:16]: 0000000000000000\n\n| k_deliver | 99 | a |\n")
+    for name, what in (("k_deliver_400k_grid608.md", "d"), ("k_update_400k.md", "u")):
+        (tmp_path / "profiles" / name).write_text(
+            "kernels.cu sha256[:16] %s.\n\n| warps active (of peak) | 28.0 %% |\n"
+            "| issue active | 27.1 %% (x) |\n" % sha)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernels_sha", lambda: sha)
+    assert bench.measured_traffic("k_deliver", "traffic_x.md") == 123456
+    assert bench.measured_traffic("k_deliver", "traffic_old.md") is None
+    assert bench.measured_traffic("k_deliver", "missing.md") is None
+    shape = bench.profiled_shape()
+    assert shape["k_deliver"]["warps_active_pct"] == 28.0
+    assert shape["k_update"]["issue_active_pct"] == 27.1
+    monkeypatch.setattr(bench, "kernels_sha", lambda: "ffffffffffffffff")
+    assert bench.profiled_shape() is None
+
+
+def test_arm_cpu_part_names():
+    import bench
+    assert bench.ARM_PARTS["0xd4f"] == "Arm Neoverse V2"
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
