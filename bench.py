@@ -332,6 +332,39 @@ def oracle_sample(args, dims, seconds=15.0, onset_steps=500):
                          onset_steps, threads)}
 
 
+def oracle_full_mid(args, onset_steps=500, timed_steps=1000):
+    """The CPU oracle (matched FP32, all-core timing variant) on the full
+    mid-size network -- the same graph, drive and seed as the GPU's mid line
+    -- over a 100 ms prefix after the onset: the full-size CPU comparison
+    for that workload (the 20 M-neuron network does not fit the oracle's
+    host memory budget)."""
+    import oracle
+    import synth
+    R, S = WORKLOAD_DIMS["mid"]
+    seed = rank_seed(0, False)
+    t0 = time.perf_counter()
+    g = synth.make_graph([S] * R, args.k_in, seed, k_within=int(round(0.8 * args.k_in)),
+                         d_within=(1, 50), d_cross=(50, 200))
+    t_gen = time.perf_counter() - t0
+    threads = args.cpu_threads if args.cpu_threads > 0 else (os.cpu_count() or 1)
+    s = oracle.Sim(g, params_for(args.rate, args.k_in), seed=seed + 1, precision=32, threads=threads)
+    s.step(onset_steps)
+    i0 = s.info()
+    t0 = time.perf_counter()
+    s.step(timed_steps)
+    wall = time.perf_counter() - t0
+    ev = s.info()["events"] - i0["events"]
+    n = g.n_neurons
+    del s, g
+    return {"value": ev / wall, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "neuron_updates_per_s": n * timed_steps / wall,
+            "rtf_of_sample": wall / (timed_steps * 1e-4), "cpu": cpu_model(), "generate_s": t_gen,
+            "sample": "%d Euler steps (%.0f ms biological) of the full mid-size network (%s "
+                      "neurons) after %d untimed steps; the matched-FP32 oracle's all-core timing "
+                      "variant on %d threads" % (timed_steps, timed_steps * 0.1, f"{n:,}",
+                                                 onset_steps, threads)}
+
+
 # Arm "CPU part" numbers of /proc/cpuinfo (Arm's published MIDR part ids)
 ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
              "0xd49": "Arm Neoverse N2"}
@@ -574,6 +607,8 @@ def run_extras(args, stream, dev):
                   "k_deliver_us": kern["k_deliver"]["avg_us"],
                   "k_deliver_frac": kern["k_deliver"]["frac"],
                   "path_frac": m["roofline"]["path"]["frac"], "clocks": m["clocks"]}
+    if not args.no_cpu_baseline:  # the oracle at full size on the host cores
+        out["mid"]["cpu_baseline"] = oracle_full_mid(args)
     # the mid-size network at the paper's other two mean rates
     out["mid_rates"] = {}
     for rate in (7, 30):
