@@ -385,7 +385,7 @@ def cpu_model():
 
 
 def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup, e2e_steps,
-                profile_steps, pageable, clocked=True):
+                profile_steps, pageable, clocked=True, extra_rates=()):
     """One network workload: generate, create, warm up, time `timed_steps`
     biological seconds (L2 flushed between them), time each kernel, and
     optionally the end-to-end path through the C ABI from host buffers.
@@ -532,6 +532,44 @@ def run_network(args, dims, stream, dev, world, rank, seed, timed_steps, warmup,
         "schedule": SCHEDULES[stats["schedule"]],
         "roofline": roof,
     }
+    # the same graph at the other mean rates: a fresh network each, one
+    # biological second of warm-up (with the tuner), two timed
+    if extra_rates:
+        out["rates"] = {}
+        r_flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        for rate in extra_rates:
+            r_net = None
+            try:
+                r_net = dbnet.Network(g, params_for(rate, args.k_in), opts, stream)
+                r_net.step(n_step)
+                r_net.sync()
+                q0 = r_net.stats()
+                r_ms = 0.0
+                for _ in range(2):
+                    with torch.cuda.stream(stream):
+                        r_flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    r_net.step(n_step)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    r_ms += a.elapsed_time(b)
+                q1 = r_net.stats()
+                r_ev = q1["events"] - q0["events"]
+                r_step = r_ms / 2
+                out["rates"]["%d_hz" % rate] = {
+                    "value": r_ev / (r_ms * 1e-3), "unit": UNIT, "rtf": r_step / (n_step * 0.1),
+                    "mean_rate_hz": (q1["spikes"] - q0["spikes"]) / g.n_neurons / 2 / (n_step * 1e-4),
+                    "steps": 2, "warmup": 1, "deliver_blocks": q1["deliver_blocks"],
+                    "schedule": SCHEDULES[q1["schedule"]],
+                    "path_frac": (upd_bytes + r_ev / 2 / n_step * (DELIVER_BYTES_PER_EVENT_TWO if two
+                                  else DELIVER_BYTES_PER_EVENT)) / (r_step / n_step * 1e-3) / 1e9 / hbm}
+            except Exception as exc:  # noqa: BLE001 -- reported in the line, the headline stands
+                out["rates"]["%d_hz" % rate] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            finally:
+                if r_net is not None:
+                    r_net.close()
+        del r_flush
     del g, keep
     return out
 
@@ -572,7 +610,9 @@ def run_ours(args):
     big_host = dims[0] * dims[1] * args.k_in * (9 if args.two_weights else 7) > 32e9
     res = run_network(args, dims, stream, dev, world, rank, rank_seed(rank, large), args.steps,
                       args.warmup, args.e2e_steps, args.profile_steps,
-                      pageable=args.pageable or big_host)
+                      pageable=args.pageable or big_host,
+                      extra_rates=tuple(r for r in (7, 30) if r != args.rate)
+                      if args.workload == "large" and not args.no_extras and world == 1 else ())
     if rank == 0:
         line = {
             "metric": METRIC, "value": res.pop("value"), "unit": UNIT, "n_gpus": world,
