@@ -71,7 +71,7 @@ static unsigned max_byte(const uint8_t* a, int64_t n) {
 
 // Host-to-device copies from pageable host memory through pinned slices:
 // the host's cores copy each slice into pinned memory while the DMA of the
-// previous slices runs (the driver's own path for pageable sources copies
+// previous slices runs (CUDA's own path for pageable sources copies
 // on one thread); pinned sources are copied directly.
 class HostStager {
  public:
